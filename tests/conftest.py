@@ -1,0 +1,28 @@
+"""Shared test configuration.
+
+Tests marked ``gpu`` need a CUDA device and the compiled CUDA library; all
+others run on the CPU (oracle pins, host logic, library exports).
+"""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU and the compiled CUDA library")
+    config.addinivalue_line("markers", "slow: long-running statistical test")
+
+
+@pytest.fixture(scope="session")
+def wn():
+    """The CUDA library binding; builds it in-tree if needed."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1005_2314_gb300 as pkg
+    return pkg
