@@ -1,0 +1,366 @@
+"""Benchmark: Wallace normal generation on one GB300 (per rank), JSON line out.
+
+Workload (one "step"): 4096 independent streams (one CTA each), pool N = 4096,
+R = 2 passes per block, seeds 1..4096 (rank r adds 4096 r), each stream
+returning its next 2^20 FP32 values -- 2^32 N(0,1) values per step written to
+HBM.  Streams persist across steps (a generator is created once and drawn
+from many times); creation (seeding, initialisation, 8 warm-up blocks) runs
+before the timed region and is reported separately.
+
+Reported: whole-job variates/s (value), the generate kernel's achieved HBM
+GB/s against the measured copy peak (roofline), the same metric delivered to
+pinned host memory through wn_generate_host (e2e), the project's own
+Box-Muller/Philox generator on the same GPU and shape (comparison), and the
+FP64 CPU oracle timed on the host's cores on a bounded sample (cpu_baseline).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 run under torch.distributed.run; ranks shard streams (weak scaling)
+and only the timing is reduced (max over ranks).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "N(0,1) variates/s on 1 GB300, % of HBM-write roofline, vs Box–Muller same GPU"
+STREAMS, POOL_N, PASSES_R, PER_STREAM = 4096, 4096, 2, 1 << 20
+WARMUP_BLOCKS = 8
+HDR_BYTES = 80
+WORKLOAD = (f"many_streams: {STREAMS} streams x pool N={POOL_N}, R={PASSES_R} passes/block, "
+            f"seeds SplitMix64(1..{STREAMS}), 2^20 FP32 variates per stream per step")
+
+
+def _config():
+    return {"workload": WORKLOAD, "streams": STREAMS, "pool_N": POOL_N, "passes_R": PASSES_R,
+            "variates_per_stream_per_step": PER_STREAM, "variates_per_step": STREAMS * PER_STREAM,
+            "output": "FP32, [stream][value] contiguous in HBM",
+            "l2": "flushed (256 MiB write) between steps, outside the per-step events; "
+                  "16 GiB of output per step also exceeds L2"}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _algorithmic_bytes(streams, per_stream):
+    """Bytes one generate launch must move: the output values plus reading and
+    writing each stream's pool and header once."""
+    return streams * (per_stream * 4 + 2 * POOL_N * 4 + 2 * HDR_BYTES)
+
+
+def _traffic_per_launch(streams, per_stream):
+    """DRAM bytes per launch from the committed ncu summary, scaled by units;
+    None when the summary is missing or the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", "generate_many_streams_traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        src = os.path.join(ROOT, "paper_1005_2314_gb300", "csrc", "wallace.cu")
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() != t["source_sha256"]:
+            return None
+        return t["dram_bytes_per_variate"] * streams * per_stream
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (test infrastructure, timed as a reported baseline)
+# ---------------------------------------------------------------------------
+
+def _cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(n_streams: int, per_stream: int, steps: int, warmup: int, threads: int):
+    """Times the FP64 oracle on `n_streams` streams of the bench workload,
+    each step returning the next `per_stream` values of every stream, spread
+    over `threads` host threads (the oracle releases the GIL).  Returns the
+    per-step times in seconds."""
+    import concurrent.futures
+    import numpy as np
+    import oracle
+
+    streams = [oracle.Stream(POOL_N, PASSES_R, seed=i + 1, warmup=WARMUP_BLOCKS) for i in range(n_streams)]
+    bufs = [np.empty(per_stream, dtype=np.float64) for _ in range(threads)]
+    groups = [streams[t::threads] for t in range(threads)]
+    lib = oracle.lib()
+
+    def work(t):
+        buf = bufs[t]
+        for s in groups[t]:
+            lib.orc_generate(s._h, buf.ctypes.data, per_stream)
+
+    times = []
+    with concurrent.futures.ThreadPoolExecutor(max_workers=threads) as ex:
+        for i in range(warmup + steps):
+            t0 = time.perf_counter()
+            list(ex.map(work, range(threads)))
+            dt = time.perf_counter() - t0
+            if i >= warmup:
+                times.append(dt)
+    return times
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1005_2314_gb300 as wn
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    seeds = [rank * STREAMS + i + 1 for i in range(STREAMS)]
+
+    t0 = time.perf_counter()
+    h = wn.wn_create_streams([POOL_N] * STREAMS, [PASSES_R] * STREAMS, seeds, WARMUP_BLOCKS, stream)
+    create_s = time.perf_counter() - t0
+    out = torch.empty(STREAMS * PER_STREAM, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        wn.wn_generate_ex(out, PER_STREAM, h, wn.WN_F32, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    variates = STREAMS * PER_STREAM
+    value = world * variates * args.steps / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+
+    # roofline of the generate kernel (the step is exactly one launch of it)
+    peak, peak_kind = _peaks()
+    algo = _algorithmic_bytes(STREAMS, PER_STREAM)
+    achieved = algo / (ms_per_step / 1e3) / 1e9
+    traffic = _traffic_per_launch(STREAMS, PER_STREAM)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_launch": algo, "kernel": "wn::generate_kernel<4, float>"}
+
+    # the conventional comparison on the same GPU and shape
+    bm_out = out
+    for _ in range(3):
+        wn.wn_boxmuller(bm_out, PER_STREAM, STREAMS, 1, wn.WN_F32, stream)
+    bm_ms = []
+    for i in range(max(5, args.steps // 2)):
+        flush.fill_(i & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        wn.wn_boxmuller(bm_out, PER_STREAM, STREAMS, 1, wn.WN_F32, stream)
+        b.record(stream)
+        bm_ms.append((a, b))
+    torch.cuda.synchronize()
+    bm_step = sum(a.elapsed_time(b) for a, b in bm_ms) / len(bm_ms)
+    bm_value = variates / (bm_step / 1e3)
+
+    # e2e: values delivered to pinned host memory through the public API
+    e2e = None
+    try:
+        host = torch.empty(STREAMS * PER_STREAM, dtype=torch.float32, pin_memory=True)
+        wn.wn_generate_host(host, PER_STREAM, h, wn.WN_F32, stream)
+        torch.cuda.synchronize()
+        e_steps = max(3, min(args.steps, 10))
+        t = time.perf_counter()
+        for _ in range(e_steps):
+            wn.wn_generate_host(host, PER_STREAM, h, wn.WN_F32, stream)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        if world > 1:
+            tt = torch.tensor([dt], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            dt = float(tt.item())
+        e2e = {"value": world * variates * e_steps / dt, "unit": "variates/s", "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": variates * 4, "steps": e_steps,
+               "how": "wn_generate_host into pinned host memory: generation in 256 MiB chunks with "
+                      "D2H copies overlapped on a second stream; host wall clock"}
+        del host
+    except Exception as ex:  # pinned allocation can fail on small hosts
+        e2e = {"value": None, "unit": "variates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+               "error": str(ex)[:200]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = _cpu_cores()
+        ns, per = 1024, PER_STREAM
+        times = oracle_sample(ns, per, steps=1, warmup=0, threads=cores)
+        cpu = {"value": ns * per / times[0], "unit": "variates/s", "cores": cores, "kind": "oracle",
+               "sample": f"{ns} of the {STREAMS} streams, next 2^20 values each after creation "
+                         f"(1/4 of one step), FP64 oracle, {cores} threads"}
+
+    line = {"metric": METRIC, "value": value, "unit": "variates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+            "clocks": clk.summary(),
+            "comparison": {"boxmuller_philox4x32_10": {"value": bm_value, "unit": "variates/s",
+                                                       "ms_per_step": bm_step,
+                                                       "wallace_over_boxmuller": value / world / bm_value}},
+            "create_s": create_s}
+    wn.wn_destroy(h)
+    return line
+
+
+def run_reference(args, rank, world):
+    """The oracle on the host's cores: same metric and workload, each step a
+    bounded sample (256 of the 4096 streams, their next 2^20 values)."""
+    if rank != 0:
+        return None
+    cores = _cpu_cores()
+    ns = 256
+    times = oracle_sample(ns, PER_STREAM, steps=args.steps, warmup=args.warmup, threads=cores)
+    total = sum(times)
+    value = ns * PER_STREAM * args.steps / total
+    sample = (f"each step: {ns} of the {STREAMS} streams, their next 2^20 values (1/16 of the workload), "
+              f"FP64 oracle over {cores} host threads")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "variates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(),
+            "cpu_baseline": {"value": value, "unit": "variates/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "variates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+
+    import __graft_entry__
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+        if rank == 0:
+            __graft_entry__.build()
+        torch.distributed.barrier()
+    else:
+        __graft_entry__.build()
+    line = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,163 @@
+/*
+ * wallace_gb300.h -- C ABI of the GB300 (sm_103a) implementation of Wallace's
+ * maximum-entropy normal generator, as discussed by R. P. Brent,
+ * "Some Comments on C. S. Wallace's Random Number Generators"
+ * (arXiv:1005.2314), Section 5.
+ *
+ * The method (Section 5.1): a pool of N values that are (nearly) iid N(0,1)
+ * is renewed by an orthogonal map, which keeps an iid N(0,1) vector iid
+ * N(0,1).  Each pass applies random-signed 4x4 blocks y_k = t - a_k,
+ * t = (a_0+a_1+a_2+a_3)/2 (Section 5.3, the printed A_1 up to row order and
+ * signs; Section 5.2 for the signs) to quadruples gathered through an affine
+ * permutation j -> alpha*j + gamma mod N with alpha odd (Section 5.4), and
+ * writes the pool transposed.  After R passes a block returns N-1 values,
+ * scaled so that the pool's sum of squares is a chi-squared_N sample drawn
+ * from the value held back by the previous block (Section 5.5, fastnorm2,
+ * approximation (c)).  A uniform generator (xorshift64 + Weyl, seeded by
+ * SplitMix64) is used only for initialisation and to choose each pass's
+ * permutation and signs, two 64-bit draws per pass (Section 5.8).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named `out` are DEVICE pointers owned by the caller (e.g. a
+ *    torch tensor's data_ptr()), aligned to 16 bytes, holding at least the
+ *    number of elements the call writes.  Host arrays are named host_*.
+ *  - `cuda_stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  Generation calls are asynchronous on that stream;
+ *    host-visible bookkeeping advances when the call is enqueued.
+ *  - Return codes: WN_OK on success; WN_EINVAL for bad arguments (nothing is
+ *    launched); WN_ENOMEM when device memory cannot be allocated; WN_ECUDA when
+ *    a CUDA call fails (the text is kept for wn_last_error()).
+ *  - A handle is not thread-safe: calls on one handle must not overlap.
+ */
+#ifndef WALLACE_GB300_H
+#define WALLACE_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wn_stream wn_stream; /* opaque: owns the device pools and generator states */
+
+typedef enum {
+    WN_OK = 0,
+    WN_EINVAL = 1,
+    WN_ENOMEM = 2,
+    WN_ECUDA = 3,
+    WN_ETIMEOUT = 4
+} wn_status;
+
+typedef enum {
+    WN_F32 = 0,  /* float, 4 bytes per value */
+    WN_BF16 = 1, /* bfloat16, round-to-nearest-even from the FP32 value */
+    WN_F16 = 2   /* IEEE half, round-to-nearest-even from the FP32 value */
+} wn_dtype;
+
+#define WN_MIN_POOL 4u
+#define WN_MAX_POOL 16384u
+#define WN_MAX_PASSES 64u
+#define WN_DEFAULT_WARMUP 8u
+
+/*
+ * wn_create -- one stream with pool size pool_N (a power of two in
+ * [WN_MIN_POOL, WN_MAX_POOL]; fastnorm's is 1024, Section 5.4), passes_R
+ * passes per block (1..WN_MAX_PASSES) and a 64-bit seed.  The pool is
+ * initialised from the uniform generator (Section 5.8) and WN_DEFAULT_WARMUP
+ * blocks are discarded.  Blocks the calling thread until the state is ready.
+ * Returns NULL on error (see wn_last_error()).
+ */
+wn_stream *wn_create(uint32_t pool_N, uint32_t passes_R, uint64_t seed);
+
+/*
+ * wn_create_streams -- n_streams independent streams in one handle: stream i
+ * has pool size pool_N[i], passes passes_R[i] and seed seeds[i] (host arrays
+ * of n_streams entries), and warmup_blocks discarded blocks (0 leaves the
+ * freshly initialised pool, for tests).  Each stream is a separate serial
+ * chain (Section 5.1); streams share nothing.  The initialisation kernels run
+ * on cuda_stream and the call synchronises it before returning.
+ * Returns NULL on error.
+ */
+wn_stream *wn_create_streams(uint32_t n_streams, const uint32_t *pool_N, const uint32_t *passes_R,
+                             const uint64_t *seeds, uint32_t warmup_blocks, void *cuda_stream);
+
+/* wn_destroy -- frees the handle's device memory (synchronises the device
+ * first).  NULL is accepted. */
+void wn_destroy(wn_stream *s);
+
+/*
+ * wn_generate -- the next `count` values of every stream of `s`, FP32, on the
+ * handle's CUDA stream (wn_set_cuda_stream; default NULL).  Stream i writes
+ * out[i*count .. i*count + count).  Each stream's values continue its
+ * sequence: the concatenation of successive calls equals one call of the
+ * summed count (blocks are cut anywhere; Section 5.5's N-1 values per block).
+ */
+wn_status wn_generate(void *out, uint64_t count, wn_stream *s);
+
+/* wn_generate_ex -- as wn_generate, with the output type and CUDA stream
+ * given explicitly. */
+wn_status wn_generate_ex(void *out, uint64_t count, wn_stream *s, wn_dtype dtype, void *cuda_stream);
+
+/*
+ * wn_generate_host -- as wn_generate_ex, but the values land in HOST memory:
+ * stream i's values go to host_out[i*count .. i*count + count) (elements of
+ * `dtype`).  The library generates in chunks into a device staging area the
+ * handle owns (allocated on first use, two buffers of at most 256 MiB) and
+ * copies each chunk to the host on a second CUDA stream while the next chunk
+ * is generated.  host_out should be page-locked (cudaHostAlloc or a pinned
+ * torch tensor) for full copy speed.  Asynchronous on cuda_stream: the
+ * values are in place once cuda_stream has been synchronised.
+ */
+wn_status wn_generate_host(void *host_out, uint64_t count, wn_stream *s, wn_dtype dtype, void *cuda_stream);
+
+/* wn_set_cuda_stream -- CUDA stream used by wn_generate. */
+wn_status wn_set_cuda_stream(wn_stream *s, void *cuda_stream);
+
+/* wn_num_streams -- number of streams in the handle (0 for NULL). */
+uint32_t wn_num_streams(const wn_stream *s);
+
+/*
+ * wn_get_pool -- copies stream i's current pool (pool_N floats, in the
+ * library's own scaling: its sum of squares is N up to rounding) to
+ * host_out.  Synchronises the handle's CUDA stream.
+ */
+wn_status wn_get_pool(const wn_stream *s, uint32_t i, float *host_out);
+
+/*
+ * wn_get_state -- stream i's generator words host_xw[0..1] (xorshift, Weyl),
+ * the reserved value r of the last block (Section 5.5), the scale of the
+ * last block, the number k of that block's values already returned, and the
+ * number of blocks completed.  Any output pointer may be NULL.
+ * Synchronises the handle's CUDA stream.
+ */
+wn_status wn_get_state(const wn_stream *s, uint32_t i, uint64_t *host_xw, double *host_r,
+                       float *host_scale, uint32_t *host_k, uint64_t *host_blocks);
+
+/*
+ * wn_rng_draws -- the first n 64-bit draws of the stream generator seeded by
+ * `seed` (SplitMix64 seeding, xorshift64 (13,7,17) + Weyl), computed on the
+ * device and copied to host_out.  For checking the integer stream
+ * (Section 5.8).  Synchronous.
+ */
+wn_status wn_rng_draws(uint64_t seed, uint64_t n, uint64_t *host_out);
+
+/*
+ * wn_boxmuller -- the conventional comparison method (Section 4; Section 5
+ * names Box-Muller): `count` normals for each of n_streams streams, stream i
+ * writing out[i*count ..).  Value j of stream i is component j mod 2 of pair
+ * (j mod 4)/2 of Philox4x32-10 block j/4 with counter (j/4 low, j/4 high, i, 0)
+ * and key (seed low, seed high): u1 = ((w >> 8) + 1) 2^-24,
+ * u2 = (w' >> 8) 2^-24, rho = sqrt(-2 ln u1), (rho cos 2 pi u2,
+ * rho sin 2 pi u2).  Computed in FP32 and stored as `dtype`.
+ */
+wn_status wn_boxmuller(void *out, uint64_t count, uint32_t n_streams, uint64_t seed,
+                       wn_dtype dtype, void *cuda_stream);
+
+/* wn_last_error -- text of the last error on the calling thread ("" if none). */
+const char *wn_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WALLACE_GB300_H */

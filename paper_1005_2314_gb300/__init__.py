@@ -1,0 +1,217 @@
+"""GB300 (sm_103a) Wallace maximum-entropy normal generator.
+
+A thin ctypes binding over the C ABI in ``include/wallace_gb300.h``: the
+functions here have the same names and only marshal arguments (torch tensors
+to device pointers, torch streams to cudaStream_t).  All generation runs in
+the CUDA kernels of ``libwallace_gb300.so``; there is no CPU path.  PyTorch
+supplies device memory and streams.
+
+The method (Brent, arXiv:1005.2314, Section 5): a pool of N normal values is
+renewed pass by pass with random-signed 4x4 orthogonal updates on permuted
+quadruples; each block of R passes returns N-1 values scaled so that the
+pool's sum of squares is a chi-squared_N sample.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "WN_F32", "WN_BF16", "WN_F16", "WnError",
+    "wn_create", "wn_create_streams", "wn_destroy", "wn_generate", "wn_generate_ex",
+    "wn_generate_host",
+    "wn_set_cuda_stream", "wn_num_streams", "wn_get_pool", "wn_get_state",
+    "wn_rng_draws", "wn_boxmuller", "wn_last_error", "library_path",
+]
+
+WN_F32, WN_BF16, WN_F16 = 0, 1, 2
+WN_OK, WN_EINVAL, WN_ENOMEM, WN_ECUDA, WN_ETIMEOUT = 0, 1, 2, 3, 4
+_STATUS = {1: "WN_EINVAL", 2: "WN_ENOMEM", 3: "WN_ECUDA", 4: "WN_ETIMEOUT"}
+
+_u32, _u64, _p, _i = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int
+
+
+class WnError(RuntimeError):
+    """A wn_* call returned an error status."""
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(_build.LIB):
+        raise ImportError(
+            f"CUDA library {_build.LIB} is missing: build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+    L = ctypes.CDLL(_build.LIB)
+    sig = {
+        "wn_create": (_p, [_u32, _u32, _u64]),
+        "wn_create_streams": (_p, [_u32, _p, _p, _p, _u32, _p]),
+        "wn_destroy": (None, [_p]),
+        "wn_generate": (_i, [_p, _u64, _p]),
+        "wn_generate_ex": (_i, [_p, _u64, _p, _i, _p]),
+        "wn_generate_host": (_i, [_p, _u64, _p, _i, _p]),
+        "wn_set_cuda_stream": (_i, [_p, _p]),
+        "wn_num_streams": (_u32, [_p]),
+        "wn_get_pool": (_i, [_p, _u32, _p]),
+        "wn_get_state": (_i, [_p, _u32, _p, _p, _p, _p, _p]),
+        "wn_rng_draws": (_i, [_u64, _u64, _p]),
+        "wn_boxmuller": (_i, [_p, _u64, _u32, _u64, _i, _p]),
+        "wn_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+_lib = _load()
+
+_DTYPE_BYTES = {WN_F32: 4, WN_BF16: 2, WN_F16: 2}
+
+
+def _torch_dtype(dt):
+    import torch
+    return {WN_F32: torch.float32, WN_BF16: torch.bfloat16, WN_F16: torch.float16}[dt]
+
+
+def _stream_ptr(cuda_stream):
+    """cudaStream_t as an int: None -> torch's current stream."""
+    if cuda_stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(cuda_stream, int):
+        return cuda_stream
+    return cuda_stream.cuda_stream
+
+
+def _out_ptr(out, need_elems: int, dtype: int) -> int:
+    """Device pointer of `out` (a CUDA tensor or an int address)."""
+    if isinstance(out, int):
+        return out
+    import torch
+    if not isinstance(out, torch.Tensor) or not out.is_cuda:
+        raise TypeError("out must be a CUDA tensor or a device address")
+    if not out.is_contiguous():
+        raise ValueError("out must be contiguous")
+    if out.dtype != _torch_dtype(dtype):
+        raise TypeError(f"out has dtype {out.dtype}, expected {_torch_dtype(dtype)}")
+    if out.numel() < need_elems:
+        raise ValueError(f"out holds {out.numel()} elements, the call writes {need_elems}")
+    return out.data_ptr()
+
+
+def _check(st: int, what: str):
+    if st != WN_OK:
+        msg = _lib.wn_last_error().decode(errors="replace")
+        raise WnError(f"{what}: {_STATUS.get(st, st)}: {msg}")
+
+
+def wn_last_error() -> str:
+    return _lib.wn_last_error().decode(errors="replace")
+
+
+class Handle:
+    """An opaque wn_stream*; freed by wn_destroy (or when collected)."""
+
+    def __init__(self, ptr: int, n: int):
+        self.ptr = ptr
+        self.n = n
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            _lib.wn_destroy(self.ptr)
+            self.ptr = None
+
+
+def wn_create(pool_N: int, passes_R: int, seed: int) -> Handle:
+    h = _lib.wn_create(pool_N, passes_R, seed)
+    if not h:
+        raise WnError(f"wn_create: {wn_last_error()}")
+    return Handle(h, 1)
+
+
+def wn_create_streams(pool_N, passes_R, seeds, warmup_blocks: int = 8, cuda_stream=None) -> Handle:
+    seeds = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+    n = seeds.size
+    N = np.ascontiguousarray(np.broadcast_to(np.asarray(pool_N, dtype=np.uint32), (n,)))
+    R = np.ascontiguousarray(np.broadcast_to(np.asarray(passes_R, dtype=np.uint32), (n,)))
+    h = _lib.wn_create_streams(n, N.ctypes.data, R.ctypes.data, seeds.ctypes.data,
+                               warmup_blocks, _stream_ptr(cuda_stream))
+    if not h:
+        raise WnError(f"wn_create_streams: {wn_last_error()}")
+    return Handle(h, n)
+
+
+def wn_destroy(h: Handle) -> None:
+    if h.ptr:
+        _lib.wn_destroy(h.ptr)
+        h.ptr = None
+
+
+def wn_generate(out, count: int, h: Handle) -> None:
+    _check(_lib.wn_generate(_out_ptr(out, count * h.n, WN_F32), count, h.ptr), "wn_generate")
+
+
+def wn_generate_ex(out, count: int, h: Handle, dtype: int = WN_F32, cuda_stream=None) -> None:
+    _check(_lib.wn_generate_ex(_out_ptr(out, count * h.n, dtype), count, h.ptr, dtype,
+                               _stream_ptr(cuda_stream)), "wn_generate_ex")
+
+
+def wn_generate_host(host_out, count: int, h: Handle, dtype: int = WN_F32, cuda_stream=None) -> None:
+    """host_out: a CPU tensor (pinned for full speed) or a host address."""
+    if isinstance(host_out, int):
+        ptr = host_out
+    else:
+        import torch
+        if not isinstance(host_out, torch.Tensor) or host_out.is_cuda or not host_out.is_contiguous():
+            raise TypeError("host_out must be a contiguous CPU tensor or a host address")
+        if host_out.dtype != _torch_dtype(dtype):
+            raise TypeError(f"host_out has dtype {host_out.dtype}, expected {_torch_dtype(dtype)}")
+        if host_out.numel() < count * h.n:
+            raise ValueError(f"host_out holds {host_out.numel()} elements, the call writes {count * h.n}")
+        ptr = host_out.data_ptr()
+    _check(_lib.wn_generate_host(ptr, count, h.ptr, dtype, _stream_ptr(cuda_stream)), "wn_generate_host")
+
+
+def wn_set_cuda_stream(h: Handle, cuda_stream) -> None:
+    _check(_lib.wn_set_cuda_stream(h.ptr, _stream_ptr(cuda_stream)), "wn_set_cuda_stream")
+
+
+def wn_num_streams(h: Handle) -> int:
+    return _lib.wn_num_streams(h.ptr)
+
+
+def wn_get_pool(h: Handle, i: int, N: int) -> np.ndarray:
+    out = np.empty(N, dtype=np.float32)
+    _check(_lib.wn_get_pool(h.ptr, i, out.ctypes.data), "wn_get_pool")
+    return out
+
+
+def wn_get_state(h: Handle, i: int) -> dict:
+    xw = np.zeros(2, dtype=np.uint64)
+    r = ctypes.c_double()
+    sc = ctypes.c_float()
+    k = ctypes.c_uint32()
+    b = ctypes.c_uint64()
+    _check(_lib.wn_get_state(h.ptr, i, xw.ctypes.data, ctypes.addressof(r), ctypes.addressof(sc),
+                             ctypes.addressof(k), ctypes.addressof(b)), "wn_get_state")
+    return {"x": int(xw[0]), "w": int(xw[1]), "r": r.value, "scale": sc.value,
+            "k": k.value, "blocks": b.value}
+
+
+def wn_rng_draws(seed: int, n: int) -> np.ndarray:
+    out = np.zeros(n, dtype=np.uint64)
+    _check(_lib.wn_rng_draws(seed, n, out.ctypes.data), "wn_rng_draws")
+    return out
+
+
+def wn_boxmuller(out, count: int, n_streams: int, seed: int, dtype: int = WN_F32, cuda_stream=None) -> None:
+    _check(_lib.wn_boxmuller(_out_ptr(out, count * n_streams, dtype), count, n_streams, seed, dtype,
+                             _stream_ptr(cuda_stream)), "wn_boxmuller")

@@ -1,0 +1,82 @@
+// wn_device.cuh -- device-side pieces of the Wallace generator for sm_103a.
+//
+// Brent, arXiv:1005.2314, Section 5: a pool of N normal values renewed by
+// random-signed 4x4 orthogonal updates on permuted quadruples, with a
+// chi-squared rescale per block.  This header holds the per-stream state
+// layout, the integer generator and the small FP64 helpers; the kernels live
+// in wallace.cu.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+namespace wn {
+
+// Per-stream state in device memory.  The pool itself lives in a separate
+// float array at pools + pool_off (16-byte aligned).
+struct __align__(16) StreamHdr {
+    uint64_t x;        // xorshift64 state (never 0); holds the seed until init
+    uint64_t w;        // Weyl state
+    double r;          // scaled reserved value of the last block (Section 5.5)
+    double A;          // chi-squared (c) constant for nu = N
+    double B;          // sqrt(2 (N - A^2))
+    uint64_t pool_off; // float offset of the pool
+    uint64_t blocks;   // blocks completed, warm-up included
+    float scale;       // output scale of the last block
+    uint32_t k;        // values of the last block already returned (N-1: none left)
+    uint32_t N;        // pool size, a power of two
+    uint32_t R;        // passes per block
+};
+static_assert(sizeof(StreamHdr) == 80, "StreamHdr layout");
+
+constexpr uint64_t kGoldenGamma = 0x9E3779B97F4A7C15ull;
+constexpr uint64_t kWeyl = 0x61C8864680B583EBull;  // 2^64 - kGoldenGamma, odd
+
+// SplitMix64 (Steele, Lea and Flood 2014): one step on `s`.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t &s)
+{
+    s += kGoldenGamma;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// One draw: xorshift64 with shifts (13, 7, 17), Weyl step, sum mod 2^64.
+__device__ __forceinline__ uint64_t draw(uint64_t &x, uint64_t &w)
+{
+    x ^= x << 13;
+    x ^= x >> 7;
+    x ^= x << 17;
+    w += kWeyl;
+    return x + w;
+}
+
+// Seed the generator: first SplitMix64 output is the xorshift state (1 if
+// it is 0), the second the Weyl state.
+__device__ __forceinline__ void seed_gen(uint64_t seed, uint64_t &x, uint64_t &w)
+{
+    uint64_t sm = seed;
+    x = splitmix64(sm);
+    if (x == 0) x = 1;
+    w = splitmix64(sm);
+}
+
+// 1/sqrt(p) in FP64: FP32 seed refined by one Newton-Raphson step
+// y <- y (1 + (1 - p y^2)/2), which squares the seed's relative error
+// (about 1e-7 -> 1e-14).  p must be positive and within FP32 range.
+__device__ __forceinline__ double rsqrt_nr(double p)
+{
+    const double y = (double)rsqrtf((float)p);
+    const double e = fma(-p, y * y, 1.0);
+    return fma(0.5 * y, e, y);
+}
+
+template <typename T> __device__ __forceinline__ T to_out(float v);
+template <> __device__ __forceinline__ float to_out<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 to_out<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ __half to_out<__half>(float v) { return __float2half_rn(v); }
+
+}  // namespace wn

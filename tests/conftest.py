@@ -24,5 +24,7 @@ def wn():
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
+    from paper_1005_2314_gb300 import build
+    build.build()
     import paper_1005_2314_gb300 as pkg
     return pkg
