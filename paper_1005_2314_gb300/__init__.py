@@ -25,7 +25,7 @@ __all__ = [
     "wn_create", "wn_create_streams", "wn_destroy", "wn_generate", "wn_generate_ex",
     "wn_generate_host",
     "wn_set_cuda_stream", "wn_num_streams", "wn_get_pool", "wn_get_state",
-    "wn_rng_draws", "wn_boxmuller", "wn_last_error", "library_path",
+    "wn_rng_draws", "wn_boxmuller", "wn_last_error", "library_path", "load",
 ]
 
 WN_F32, WN_BF16, WN_F16 = 0, 1, 2
@@ -71,14 +71,31 @@ def _load() -> ctypes.CDLL:
     return L
 
 
-_lib = _load()
+_lib_handle = None
+
+
+def _L() -> ctypes.CDLL:
+    """The loaded library; raises ImportError when it has not been built."""
+    global _lib_handle
+    if _lib_handle is None:
+        _lib_handle = _load()
+    return _lib_handle
+
+
+def load() -> str:
+    """Loads the CUDA library now (raises if it is missing); returns its path."""
+    _L()
+    return _build.LIB
 
 _DTYPE_BYTES = {WN_F32: 4, WN_BF16: 2, WN_F16: 2}
 
 
 def _torch_dtype(dt):
     import torch
-    return {WN_F32: torch.float32, WN_BF16: torch.bfloat16, WN_F16: torch.float16}[dt]
+    m = {WN_F32: torch.float32, WN_BF16: torch.bfloat16, WN_F16: torch.float16}
+    if dt not in m:
+        raise ValueError(f"unknown wn_dtype {dt}")
+    return m[dt]
 
 
 def _stream_ptr(cuda_stream):
@@ -109,12 +126,12 @@ def _out_ptr(out, need_elems: int, dtype: int) -> int:
 
 def _check(st: int, what: str):
     if st != WN_OK:
-        msg = _lib.wn_last_error().decode(errors="replace")
+        msg = _L().wn_last_error().decode(errors="replace")
         raise WnError(f"{what}: {_STATUS.get(st, st)}: {msg}")
 
 
 def wn_last_error() -> str:
-    return _lib.wn_last_error().decode(errors="replace")
+    return _L().wn_last_error().decode(errors="replace")
 
 
 class Handle:
@@ -126,12 +143,12 @@ class Handle:
 
     def __del__(self):
         if getattr(self, "ptr", None):
-            _lib.wn_destroy(self.ptr)
+            _L().wn_destroy(self.ptr)
             self.ptr = None
 
 
 def wn_create(pool_N: int, passes_R: int, seed: int) -> Handle:
-    h = _lib.wn_create(pool_N, passes_R, seed)
+    h = _L().wn_create(pool_N, passes_R, seed)
     if not h:
         raise WnError(f"wn_create: {wn_last_error()}")
     return Handle(h, 1)
@@ -142,7 +159,7 @@ def wn_create_streams(pool_N, passes_R, seeds, warmup_blocks: int = 8, cuda_stre
     n = seeds.size
     N = np.ascontiguousarray(np.broadcast_to(np.asarray(pool_N, dtype=np.uint32), (n,)))
     R = np.ascontiguousarray(np.broadcast_to(np.asarray(passes_R, dtype=np.uint32), (n,)))
-    h = _lib.wn_create_streams(n, N.ctypes.data, R.ctypes.data, seeds.ctypes.data,
+    h = _L().wn_create_streams(n, N.ctypes.data, R.ctypes.data, seeds.ctypes.data,
                                warmup_blocks, _stream_ptr(cuda_stream))
     if not h:
         raise WnError(f"wn_create_streams: {wn_last_error()}")
@@ -151,16 +168,16 @@ def wn_create_streams(pool_N, passes_R, seeds, warmup_blocks: int = 8, cuda_stre
 
 def wn_destroy(h: Handle) -> None:
     if h.ptr:
-        _lib.wn_destroy(h.ptr)
+        _L().wn_destroy(h.ptr)
         h.ptr = None
 
 
 def wn_generate(out, count: int, h: Handle) -> None:
-    _check(_lib.wn_generate(_out_ptr(out, count * h.n, WN_F32), count, h.ptr), "wn_generate")
+    _check(_L().wn_generate(_out_ptr(out, count * h.n, WN_F32), count, h.ptr), "wn_generate")
 
 
 def wn_generate_ex(out, count: int, h: Handle, dtype: int = WN_F32, cuda_stream=None) -> None:
-    _check(_lib.wn_generate_ex(_out_ptr(out, count * h.n, dtype), count, h.ptr, dtype,
+    _check(_L().wn_generate_ex(_out_ptr(out, count * h.n, dtype), count, h.ptr, dtype,
                                _stream_ptr(cuda_stream)), "wn_generate_ex")
 
 
@@ -177,20 +194,20 @@ def wn_generate_host(host_out, count: int, h: Handle, dtype: int = WN_F32, cuda_
         if host_out.numel() < count * h.n:
             raise ValueError(f"host_out holds {host_out.numel()} elements, the call writes {count * h.n}")
         ptr = host_out.data_ptr()
-    _check(_lib.wn_generate_host(ptr, count, h.ptr, dtype, _stream_ptr(cuda_stream)), "wn_generate_host")
+    _check(_L().wn_generate_host(ptr, count, h.ptr, dtype, _stream_ptr(cuda_stream)), "wn_generate_host")
 
 
 def wn_set_cuda_stream(h: Handle, cuda_stream) -> None:
-    _check(_lib.wn_set_cuda_stream(h.ptr, _stream_ptr(cuda_stream)), "wn_set_cuda_stream")
+    _check(_L().wn_set_cuda_stream(h.ptr, _stream_ptr(cuda_stream)), "wn_set_cuda_stream")
 
 
 def wn_num_streams(h: Handle) -> int:
-    return _lib.wn_num_streams(h.ptr)
+    return _L().wn_num_streams(h.ptr)
 
 
 def wn_get_pool(h: Handle, i: int, N: int) -> np.ndarray:
     out = np.empty(N, dtype=np.float32)
-    _check(_lib.wn_get_pool(h.ptr, i, out.ctypes.data), "wn_get_pool")
+    _check(_L().wn_get_pool(h.ptr, i, out.ctypes.data), "wn_get_pool")
     return out
 
 
@@ -200,7 +217,7 @@ def wn_get_state(h: Handle, i: int) -> dict:
     sc = ctypes.c_float()
     k = ctypes.c_uint32()
     b = ctypes.c_uint64()
-    _check(_lib.wn_get_state(h.ptr, i, xw.ctypes.data, ctypes.addressof(r), ctypes.addressof(sc),
+    _check(_L().wn_get_state(h.ptr, i, xw.ctypes.data, ctypes.addressof(r), ctypes.addressof(sc),
                              ctypes.addressof(k), ctypes.addressof(b)), "wn_get_state")
     return {"x": int(xw[0]), "w": int(xw[1]), "r": r.value, "scale": sc.value,
             "k": k.value, "blocks": b.value}
@@ -208,10 +225,10 @@ def wn_get_state(h: Handle, i: int) -> dict:
 
 def wn_rng_draws(seed: int, n: int) -> np.ndarray:
     out = np.zeros(n, dtype=np.uint64)
-    _check(_lib.wn_rng_draws(seed, n, out.ctypes.data), "wn_rng_draws")
+    _check(_L().wn_rng_draws(seed, n, out.ctypes.data), "wn_rng_draws")
     return out
 
 
 def wn_boxmuller(out, count: int, n_streams: int, seed: int, dtype: int = WN_F32, cuda_stream=None) -> None:
-    _check(_lib.wn_boxmuller(_out_ptr(out, count * n_streams, dtype), count, n_streams, seed, dtype,
+    _check(_L().wn_boxmuller(_out_ptr(out, count * n_streams, dtype), count, n_streams, seed, dtype,
                              _stream_ptr(cuda_stream)), "wn_boxmuller")

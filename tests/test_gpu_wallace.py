@@ -230,7 +230,7 @@ def test_argument_errors(wn, torch):
     with pytest.raises(wn.WnError):
         wn.wn_generate_ex(buf[1:].data_ptr(), 10, h)  # not 16-byte aligned
     with pytest.raises(wn.WnError):
-        wn.wn_generate_ex(buf, 10, h, 7)
+        wn.wn_generate_ex(buf.data_ptr(), 10, h, 7)  # unknown dtype, rejected by the C ABI
     with pytest.raises(wn.WnError):
         wn.wn_create(48, 2, 1)
     with pytest.raises(wn.WnError):
