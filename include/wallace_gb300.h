@@ -113,6 +113,20 @@ wn_status wn_generate_host(void *host_out, uint64_t count, wn_stream *s, wn_dtyp
 /* wn_set_cuda_stream -- CUDA stream used by wn_generate. */
 wn_status wn_set_cuda_stream(wn_stream *s, void *cuda_stream);
 
+/*
+ * wn_set_config -- launch shape of the handle's generate kernel: `threads`
+ * per CTA (a multiple of 32) each updating `quads_per_thread` quadruples per
+ * pass, with threads * quads_per_thread >= pool_N/4 for the handle's largest
+ * pool.  (0, 0) restores the default.  The shape changes only the order of
+ * the FP32 partial sums of squares, so outputs stay within the same FP32
+ * tolerance of the oracle; integer streams are unaffected.  WN_EINVAL if no
+ * compiled kernel has that shape.
+ */
+wn_status wn_set_config(wn_stream *s, uint32_t quads_per_thread, uint32_t threads);
+
+/* wn_get_config -- the launch shape the next generate call will use. */
+wn_status wn_get_config(const wn_stream *s, uint32_t *quads_per_thread, uint32_t *threads);
+
 /* wn_num_streams -- number of streams in the handle (0 for NULL). */
 uint32_t wn_num_streams(const wn_stream *s);
 

@@ -24,7 +24,7 @@ __all__ = [
     "WN_F32", "WN_BF16", "WN_F16", "WnError",
     "wn_create", "wn_create_streams", "wn_destroy", "wn_generate", "wn_generate_ex",
     "wn_generate_host",
-    "wn_set_cuda_stream", "wn_num_streams", "wn_get_pool", "wn_get_state",
+    "wn_set_cuda_stream", "wn_set_config", "wn_get_config", "wn_num_streams", "wn_get_pool", "wn_get_state",
     "wn_rng_draws", "wn_boxmuller", "wn_last_error", "library_path", "load",
 ]
 
@@ -57,6 +57,8 @@ def _load() -> ctypes.CDLL:
         "wn_generate_ex": (_i, [_p, _u64, _p, _i, _p]),
         "wn_generate_host": (_i, [_p, _u64, _p, _i, _p]),
         "wn_set_cuda_stream": (_i, [_p, _p]),
+        "wn_set_config": (_i, [_p, _u32, _u32]),
+        "wn_get_config": (_i, [_p, _p, _p]),
         "wn_num_streams": (_u32, [_p]),
         "wn_get_pool": (_i, [_p, _u32, _p]),
         "wn_get_state": (_i, [_p, _u32, _p, _p, _p, _p, _p]),
@@ -199,6 +201,17 @@ def wn_generate_host(host_out, count: int, h: Handle, dtype: int = WN_F32, cuda_
 
 def wn_set_cuda_stream(h: Handle, cuda_stream) -> None:
     _check(_L().wn_set_cuda_stream(h.ptr, _stream_ptr(cuda_stream)), "wn_set_cuda_stream")
+
+
+def wn_set_config(h: Handle, quads_per_thread: int, threads: int) -> None:
+    _check(_L().wn_set_config(h.ptr, quads_per_thread, threads), "wn_set_config")
+
+
+def wn_get_config(h: Handle) -> tuple[int, int]:
+    q = ctypes.c_uint32()
+    t = ctypes.c_uint32()
+    _check(_L().wn_get_config(h.ptr, ctypes.addressof(q), ctypes.addressof(t)), "wn_get_config")
+    return q.value, t.value
 
 
 def wn_num_streams(h: Handle) -> int:

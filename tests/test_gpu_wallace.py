@@ -235,3 +235,40 @@ def test_argument_errors(wn, torch):
         wn.wn_create(48, 2, 1)
     with pytest.raises(wn.WnError):
         wn.wn_create_streams([64, 64], [2, 0], [1, 2])
+
+
+SHAPES = {4096: [(1, 1024), (2, 512), (4, 256), (8, 128), (8, 512)],
+          16384: [(4, 1024), (8, 512)],
+          1024: [(1, 256), (1, 1024), (2, 128), (4, 64), (8, 32)]}
+
+
+@pytest.mark.parametrize("N", sorted(SHAPES))
+def test_every_launch_shape_matches_oracle(wn, torch, N):
+    # several streams and a count that is not a multiple of 4, so stream
+    # outputs start at every alignment; every shape must give the oracle's
+    # values within tolerance and the same integer state
+    R, n = 2, 5
+    count = 3 * (N - 1) + 6
+    seeds = [40 + i for i in range(n)]
+    refs = [oracle.Stream(N, R, s).generate(count) for s in seeds]
+    words = None
+    for qt, threads in SHAPES[N]:
+        h = wn.wn_create_streams([N] * n, [R] * n, seeds)
+        wn.wn_set_config(h, qt, threads)
+        assert wn.wn_get_config(h) == (qt, threads)
+        got = _gen(wn, torch, h, count).cpu().numpy().reshape(n, count)
+        for i in range(n):
+            assert_fp32_close(got[i], refs[i], passes_fresh(count, N, R), f"shape {qt}x{threads} stream {i}")
+        w = [(wn.wn_get_state(h, i)["x"], wn.wn_get_state(h, i)["w"]) for i in range(n)]
+        assert words is None or w == words
+        words = w
+
+
+def test_rejects_uncompiled_shape(wn):
+    h = wn.wn_create(4096, 2, 1)
+    with pytest.raises(wn.WnError):
+        wn.wn_set_config(h, 4, 128)   # 512 quadruples < 1024
+    with pytest.raises(wn.WnError):
+        wn.wn_set_config(h, 3, 512)
+    wn.wn_set_config(h, 0, 0)
+    assert wn.wn_get_config(h) == (4, 256)
