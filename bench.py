@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "N(0,1) variates/s on 1 GB300, % of HBM-write roofline, vs Box–Muller same GPU"
 STREAMS, POOL_N, PASSES_R, PER_STREAM = 4096, 4096, 2, 1 << 20
 WARMUP_BLOCKS = 8
-HDR_BYTES = 80
+HDR_BYTES = 96
 WORKLOAD = (f"many_streams: {STREAMS} streams x pool N={POOL_N}, R={PASSES_R} passes/block, "
             f"seeds SplitMix64(1..{STREAMS}), 2^20 FP32 variates per stream per step")
 

@@ -28,8 +28,12 @@ struct __align__(16) StreamHdr {
     uint32_t k;        // values of the last block already returned (N-1: none left)
     uint32_t N;        // pool size, a power of two
     uint32_t R;        // passes per block
+    uint32_t flags;    // nonzero: a launch could not run this stream (bit 0: shared-memory layout)
+    uint32_t pad_;
+    double sumsq;      // sum of squares of the stored pool, as the generate kernel forms it
+    uint64_t pad2_;
 };
-static_assert(sizeof(StreamHdr) == 80, "StreamHdr layout");
+static_assert(sizeof(StreamHdr) == 96, "StreamHdr layout");
 
 constexpr uint64_t kGoldenGamma = 0x9E3779B97F4A7C15ull;
 constexpr uint64_t kWeyl = 0x61C8864680B583EBull;  // 2^64 - kGoldenGamma, odd
@@ -62,16 +66,6 @@ __device__ __forceinline__ void seed_gen(uint64_t seed, uint64_t &x, uint64_t &w
     x = splitmix64(sm);
     if (x == 0) x = 1;
     w = splitmix64(sm);
-}
-
-// 1/sqrt(p) in FP64: FP32 seed refined by one Newton-Raphson step
-// y <- y (1 + (1 - p y^2)/2), which squares the seed's relative error
-// (about 1e-7 -> 1e-14).  p must be positive and within FP32 range.
-__device__ __forceinline__ double rsqrt_nr(double p)
-{
-    const double y = (double)rsqrtf((float)p);
-    const double e = fma(-p, y * y, 1.0);
-    return fma(0.5 * y, e, y);
 }
 
 template <typename T> __device__ __forceinline__ T to_out(float v);

@@ -237,9 +237,11 @@ def test_argument_errors(wn, torch):
         wn.wn_create_streams([64, 64], [2, 0], [1, 2])
 
 
-SHAPES = {4096: [(1, 1024), (2, 512), (4, 256), (8, 128), (8, 512)],
-          16384: [(4, 1024), (8, 512)],
-          1024: [(1, 256), (1, 1024), (2, 128), (4, 64), (8, 32)]}
+# (quadruples per thread, compute threads): full shapes cover the pool
+# exactly, the others leave quadruple slots idle
+SHAPES = {4096: [(2, 512), (4, 256), (8, 128), (8, 512), (16, 256)],
+          16384: [(8, 512), (16, 256)],
+          1024: [(1, 256), (1, 512), (2, 128), (4, 64), (8, 32), (16, 32)]}
 
 
 @pytest.mark.parametrize("N", sorted(SHAPES))
