@@ -38,16 +38,30 @@ METRIC = "N(0,1) variates/s on 1 GB300, % of HBM-write roofline, vs Box–Muller
 STREAMS, POOL_N, PASSES_R, PER_STREAM = 4096, 4096, 2, 1 << 20
 WARMUP_BLOCKS = 8
 HDR_BYTES = 96
-WORKLOAD = (f"many_streams: {STREAMS} streams x pool N={POOL_N}, R={PASSES_R} passes/block, "
-            f"seeds SplitMix64(1..{STREAMS}), 2^20 FP32 variates per stream per step")
+KERNEL_SOURCES = ("wn_gen.cuh", "wn_device.cuh")
 
 
-def _config():
-    return {"workload": WORKLOAD, "streams": STREAMS, "pool_N": POOL_N, "passes_R": PASSES_R,
-            "variates_per_stream_per_step": PER_STREAM, "variates_per_step": STREAMS * PER_STREAM,
+def _workload(streams, per_stream):
+    return (f"many_streams: {streams} streams x pool N={POOL_N}, R={PASSES_R} passes/block, "
+            f"seeds SplitMix64(1..{streams}), {per_stream} FP32 variates per stream per step")
+
+
+def _config(streams=STREAMS, per_stream=PER_STREAM):
+    return {"workload": _workload(streams, per_stream), "streams": streams, "pool_N": POOL_N,
+            "passes_R": PASSES_R, "variates_per_stream_per_step": per_stream,
+            "variates_per_step": streams * per_stream,
             "output": "FP32, [stream][value] contiguous in HBM",
             "l2": "flushed (256 MiB write) between steps, outside the per-step events; "
                   "16 GiB of output per step also exceeds L2"}
+
+
+def kernel_source_hash():
+    """sha256 over the generate kernel's sources (profiles record it)."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1005_2314_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def _peaks():
@@ -66,16 +80,17 @@ def _algorithmic_bytes(streams, per_stream):
 
 
 def _traffic_per_launch(streams, per_stream):
-    """DRAM bytes per launch from the committed ncu summary, scaled by units;
-    None when the summary is missing or the kernel source changed since."""
+    """DRAM bytes per launch from the committed ncu summary (a capture with the
+    same per-stream count on fewer streams, scaled by streams: every stream of
+    the launch moves the same bytes); None when the summary is missing, was
+    taken at another per-stream count, or the kernel changed since."""
     path = os.path.join(ROOT, "profiles", "generate_many_streams_traffic.json")
     try:
         with open(path) as f:
             t = json.load(f)
-        src = os.path.join(ROOT, "paper_1005_2314_gb300", "csrc", "wallace.cu")
-        if hashlib.sha256(open(src, "rb").read()).hexdigest() != t["source_sha256"]:
+        if t["source_sha256"] != kernel_source_hash() or t["per_stream"] != per_stream:
             return None
-        return t["dram_bytes_per_variate"] * streams * per_stream
+        return int(t["dram_bytes_per_stream"] * streams)
     except Exception:
         return None
 
@@ -192,11 +207,18 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
+    STREAMS, PER_STREAM = args.streams, args.per_stream
     seeds = [rank * STREAMS + i + 1 for i in range(STREAMS)]
 
     t0 = time.perf_counter()
     h = wn.wn_create_streams([POOL_N] * STREAMS, [PASSES_R] * STREAMS, seeds, WARMUP_BLOCKS, stream)
     create_s = time.perf_counter() - t0
+    if args.shape:
+        qt, th = (int(v) for v in args.shape.split(","))
+        wn.wn_set_config(h, qt, th)
+        shape = wn.wn_get_config(h)
+    else:  # the library's autotuner picks the launch shape (on a copy of the state)
+        shape = wn.wn_autotune(h, min(PER_STREAM, 1 << 17), wn.WN_F32, stream)
     out = torch.empty(STREAMS * PER_STREAM, dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
@@ -238,7 +260,27 @@ def run_ours(args, rank, world, local_rank):
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                "algorithmic_bytes_per_launch": algo, "kernel": "wn::generate_kernel<4, float>"}
+                "algorithmic_bytes_per_launch": algo,
+                "kernel": f"wn::generate_kernel (FP32 out, {shape[0]} quadruples x {shape[1]} compute threads "
+                          f"+ 1 control warp per stream)"}
+    if args.kernel_only:
+        wn.wn_destroy(h)
+        return {"metric": METRIC, "value": value, "unit": "variates/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "config": _config(STREAMS, PER_STREAM),
+                "roofline": roofline, "gpu_launches": args.steps, "kernel_only": True}
+
+    # context: a plain write of the same bytes by torch (fill_), i.e. what a
+    # write-only stream reaches on this GPU
+    fill_ms = []
+    for i in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(i & 0xFF)
+        a.record(stream)
+        out.fill_(float(i))
+        b.record(stream)
+        fill_ms.append((a, b))
+    torch.cuda.synchronize()
+    fill_gbs = out.numel() * 4 / (min(x.elapsed_time(y) for x, y in fill_ms) / 1e3) / 1e9
 
     # the conventional comparison on the same GPU and shape
     bm_out = out
@@ -292,13 +334,15 @@ def run_ours(args, rank, world, local_rank):
 
     line = {"metric": METRIC, "value": value, "unit": "variates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(),
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(STREAMS, PER_STREAM),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
             "clocks": clk.summary(),
             "comparison": {"boxmuller_philox4x32_10": {"value": bm_value, "unit": "variates/s",
                                                        "ms_per_step": bm_step,
                                                        "wallace_over_boxmuller": value / world / bm_value}},
-            "create_s": create_s}
+            "create_s": create_s,
+            "context": {"torch_fill_write_gbs": round(fill_gbs, 1),
+                        "frac_of_fill": round(achieved / fill_gbs, 4)}}
     wn.wn_destroy(h)
     return line
 
@@ -331,6 +375,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--streams", type=int, default=STREAMS, help="streams per GPU (default 4096)")
+    ap.add_argument("--per-stream", type=int, default=PER_STREAM, help="values per stream per step")
+    ap.add_argument("--shape", default="",
+                    help="launch shape 'quadruples,threads' instead of autotuning (e.g. 8,128)")
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="time only the generate steps (for ncu captures of the generate kernel)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 

@@ -124,6 +124,19 @@ wn_status wn_set_cuda_stream(wn_stream *s, void *cuda_stream);
  */
 wn_status wn_set_config(wn_stream *s, uint32_t quads_per_thread, uint32_t threads);
 
+/*
+ * wn_autotune -- times every compiled launch shape that covers the handle's
+ * pools on a saved copy of its state, generating `count` values per stream as
+ * `dtype`, and keeps the fastest for later calls (the streams' sequences are
+ * unaffected: the state is restored afterwards).  The chosen shape is
+ * returned through quads_per_thread and threads (either may be NULL).  A
+ * result is remembered per (streams, largest pool, passes, dtype, count) for
+ * the process.  Synchronous; allocates a temporary output of
+ * n_streams * count elements and a copy of the state.
+ */
+wn_status wn_autotune(wn_stream *s, uint64_t count, wn_dtype dtype, void *cuda_stream,
+                      uint32_t *quads_per_thread, uint32_t *threads);
+
 /* wn_get_config -- the launch shape the next generate call will use. */
 wn_status wn_get_config(const wn_stream *s, uint32_t *quads_per_thread, uint32_t *threads);
 

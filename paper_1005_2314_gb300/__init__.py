@@ -24,7 +24,7 @@ __all__ = [
     "WN_F32", "WN_BF16", "WN_F16", "WnError",
     "wn_create", "wn_create_streams", "wn_destroy", "wn_generate", "wn_generate_ex",
     "wn_generate_host",
-    "wn_set_cuda_stream", "wn_set_config", "wn_get_config", "wn_num_streams", "wn_get_pool", "wn_get_state",
+    "wn_set_cuda_stream", "wn_set_config", "wn_get_config", "wn_autotune", "wn_num_streams", "wn_get_pool", "wn_get_state",
     "wn_rng_draws", "wn_boxmuller", "wn_last_error", "library_path", "load",
 ]
 
@@ -59,6 +59,7 @@ def _load() -> ctypes.CDLL:
         "wn_set_cuda_stream": (_i, [_p, _p]),
         "wn_set_config": (_i, [_p, _u32, _u32]),
         "wn_get_config": (_i, [_p, _p, _p]),
+        "wn_autotune": (_i, [_p, _u64, _i, _p, _p, _p]),
         "wn_num_streams": (_u32, [_p]),
         "wn_get_pool": (_i, [_p, _u32, _p]),
         "wn_get_state": (_i, [_p, _u32, _p, _p, _p, _p, _p]),
@@ -211,6 +212,15 @@ def wn_get_config(h: Handle) -> tuple[int, int]:
     q = ctypes.c_uint32()
     t = ctypes.c_uint32()
     _check(_L().wn_get_config(h.ptr, ctypes.addressof(q), ctypes.addressof(t)), "wn_get_config")
+    return q.value, t.value
+
+
+def wn_autotune(h: Handle, count: int, dtype: int = WN_F32, cuda_stream=None) -> tuple[int, int]:
+    """Times the compiled launch shapes on a copy of the state; keeps the best."""
+    q = ctypes.c_uint32()
+    t = ctypes.c_uint32()
+    _check(_L().wn_autotune(h.ptr, count, dtype, _stream_ptr(cuda_stream), ctypes.addressof(q),
+                            ctypes.addressof(t)), "wn_autotune")
     return q.value, t.value
 
 

@@ -7,8 +7,9 @@
 // words (w0, w1) and (w2, w3) each give u1 = ((w >> 8) + 1) 2^-24 in (0, 1],
 // u2 = (w' >> 8) 2^-24 in [0, 1), rho = sqrt(-2 ln u1) and the pair
 // (rho cos 2 pi u2, rho sin 2 pi u2).  The kernel is a grid-stride loop over
-// all streams' blocks; four consecutive outputs go out as one 16-byte
-// (FP32) or 8-byte (16-bit types) store when the destination allows it.
+// each stream's blocks (grid rows are streams); four consecutive outputs go
+// out as one 16-byte (FP32) or 8-byte (16-bit types) store when the
+// destination allows it.
 #include <string>
 
 #include "wallace_gb300.h"
@@ -67,23 +68,23 @@ __global__ void __launch_bounds__(256) boxmuller_kernel(OutT *__restrict__ out, 
                                                         uint32_t n_streams, uint64_t seed)
 {
     const uint64_t mb = (count + 3) / 4;  // Philox blocks per stream
-    const uint64_t total = mb * n_streams;
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     const bool vec_ok = (count % 4 == 0) &&
                         (reinterpret_cast<uintptr_t>(out) % (4 * sizeof(OutT)) == 0);
-    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
-         g += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t stream = (uint32_t)(g / mb);
-        const uint64_t m = g - (uint64_t)stream * mb;
-        const uint4 w = philox4x32_10(make_uint4((uint32_t)m, (uint32_t)(m >> 32), stream, 0u), key);
-        const float2 p0 = bm_pair(w.x, w.y), p1 = bm_pair(w.z, w.w);
-        OutT *o = out + (uint64_t)stream * count + 4 * m;
-        if (vec_ok) {
-            Vec4<OutT>::store(o, make_float4(p0.x, p0.y, p1.x, p1.y));
-        } else {
-            const float z[4] = {p0.x, p0.y, p1.x, p1.y};
-            const uint64_t n = count - 4 * m < 4 ? count - 4 * m : 4;
-            for (uint64_t i = 0; i < n; ++i) o[i] = to_out<OutT>(z[i]);
+    for (uint32_t stream = blockIdx.y; stream < n_streams; stream += gridDim.y) {
+        OutT *os = out + (uint64_t)stream * count;
+        for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < mb;
+             m += (uint64_t)gridDim.x * blockDim.x) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)m, (uint32_t)(m >> 32), stream, 0u), key);
+            const float2 p0 = bm_pair(w.x, w.y), p1 = bm_pair(w.z, w.w);
+            OutT *o = os + 4 * m;
+            if (vec_ok) {
+                Vec4<OutT>::store(o, make_float4(p0.x, p0.y, p1.x, p1.y));
+            } else {
+                const float z[4] = {p0.x, p0.y, p1.x, p1.y};
+                const uint64_t n = count - 4 * m < 4 ? count - 4 * m : 4;
+                for (uint64_t i = 0; i < n; ++i) o[i] = to_out<OutT>(z[i]);
+            }
         }
     }
 }
@@ -105,10 +106,16 @@ extern "C" wn_status wn_boxmuller(void *out, uint64_t count, uint32_t n_streams,
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return wn::set_error(WN_ECUDA, "wn_boxmuller: no CUDA device");
-    const uint64_t total = (count + 3) / 4 * n_streams;
-    uint64_t want = (total + 255) / 256;
-    const uint64_t cap = (uint64_t)sms * 8;
-    const unsigned grid = (unsigned)(want < cap ? want : cap);
+    // blocks: one row per stream (up to 65535, then rows loop), and along a
+    // row enough blocks that the grid fills the GPU about eight CTAs per SM
+    const uint64_t mb = (count + 3) / 4;
+    const unsigned gy = n_streams < 65535u ? n_streams : 65535u;
+    const uint64_t target = (uint64_t)sms * 8;
+    uint64_t gx = (target + gy - 1) / gy;
+    const uint64_t gx_max = (mb + 255) / 256;
+    if (gx > gx_max) gx = gx_max;
+    if (gx < 1) gx = 1;
+    const dim3 grid((unsigned)gx, gy);
     switch (dtype) {
     case WN_F32: wn::boxmuller_kernel<float><<<grid, 256, 0, cs>>>((float *)out, count, n_streams, seed); break;
     case WN_BF16:

@@ -3,6 +3,9 @@
 // the stream initialisation kernel.  The generate kernel itself is in
 // wn_gen.cuh (instantiated per output type in gen_*.cu).
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -147,14 +150,15 @@ bool cfg_ok(const LaunchCfg &c, uint32_t n_max)
            (uint64_t)c.threads * c.qt >= n_max / 4;
 }
 
-// Default threads and quadruples per thread for a launch whose largest pool
-// is n_max: one quadruple per thread up to N = 1024 (at least one full
-// warp), four above.
+// Default compute threads and quadruples per thread for a launch whose
+// largest pool is n_max (measured on GB300 for 4096 streams of N = 4096, R = 2:
+// 8 quadruples x 128 threads beat 4 x 256 by 13% and 2 x 512 by 50%): one
+// quadruple per thread up to N = 1024 (at least one full warp), eight above.
 LaunchCfg pick_cfg(uint32_t n_max)
 {
     const uint32_t nq = n_max / 4;
     if (nq <= 256) return {1, 1024, std::max(32u, (nq + 31u) / 32u * 32u)};
-    if (nq <= 1024) return {4, 288, nq / 4};
+    if (nq <= 1024) return {8, 160, nq / 8};
     return {8, 544, nq / 8};
 }
 
@@ -320,6 +324,118 @@ wn_status wn_set_config(wn_stream *s, uint32_t quads_per_thread, uint32_t thread
                                    " threads covers pool " + std::to_string(s->n_max));
     s->cfg = best;
     s->has_cfg = true;
+    return WN_OK;
+}
+
+wn_status wn_autotune(wn_stream *s, uint64_t count, wn_dtype dtype, void *cuda_stream, uint32_t *quads_per_thread,
+                      uint32_t *threads)
+{
+    if (!s) return fail(WN_EINVAL, "wn_autotune: NULL handle");
+    if (count == 0) return fail(WN_EINVAL, "wn_autotune: count must be positive");
+    if (dtype != WN_F32 && dtype != WN_BF16 && dtype != WN_F16) return fail(WN_EINVAL, "wn_autotune: unknown dtype");
+    using Key = std::tuple<uint32_t, uint32_t, uint32_t, bool, int, uint64_t, int>;
+    static std::map<Key, LaunchCfg> cache;
+    static std::mutex mu;
+    const Key key{s->n, s->n_max, s->r_max, s->uniform_N, (int)dtype, count, s->device};
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            s->cfg = it->second;
+            s->has_cfg = true;
+            if (quads_per_thread) *quads_per_thread = (uint32_t)s->cfg.qt;
+            if (threads) *threads = s->cfg.threads;
+            return WN_OK;
+        }
+    }
+    // candidate shapes: every compiled one whose compute threads cover the
+    // largest pool with at most twice the needed quadruple slots
+    std::vector<LaunchCfg> cand;
+    const uint32_t nq = s->n_max / 4;
+    for (const auto &k : wn::kShapes)
+        for (uint32_t t = 32; t + 32 <= (uint32_t)k[1]; t += 32) {
+            LaunchCfg c{k[0], k[1], t};
+            const uint64_t slots = (uint64_t)t * k[0];
+            if (cfg_ok(c, s->n_max) && slots < 2ull * nq + 32ull * k[0]) {
+                bool dup = false;  // same (qt, threads) under a larger bound
+                for (auto &o : cand)
+                    if (o.qt == c.qt && o.threads == c.threads) dup = true;
+                if (!dup) cand.push_back(c);
+            }
+        }
+    if (cand.empty()) return fail(WN_EINVAL, "wn_autotune: no compiled shape fits");
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(cuda_stream);
+    const size_t esize = dtype == WN_F32 ? 4 : 2;
+    size_t pool_floats = 0;
+    for (uint32_t i = 0; i < s->n; ++i) pool_floats += s->N[i];
+    wn::StreamHdr *hdr_bak = nullptr;
+    float *pool_bak = nullptr;
+    void *tmp = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        if (hdr_bak) cudaFree(hdr_bak);
+        if (pool_bak) cudaFree(pool_bak);
+        if (tmp) cudaFree(tmp);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    cudaError_t e = cudaMalloc(&hdr_bak, sizeof(wn::StreamHdr) * s->n);
+    if (e == cudaSuccess) e = cudaMalloc(&pool_bak, sizeof(float) * pool_floats);
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, esize * count * s->n);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    auto save = [&](bool to_backup) {
+        cudaError_t r = cudaMemcpyAsync(to_backup ? (void *)hdr_bak : (void *)s->d_hdr,
+                                        to_backup ? (void *)s->d_hdr : (void *)hdr_bak,
+                                        sizeof(wn::StreamHdr) * s->n, cudaMemcpyDeviceToDevice, cs);
+        if (r == cudaSuccess)
+            r = cudaMemcpyAsync(to_backup ? (void *)pool_bak : (void *)s->d_pools,
+                                to_backup ? (void *)s->d_pools : (void *)pool_bak, sizeof(float) * pool_floats,
+                                cudaMemcpyDeviceToDevice, cs);
+        return r;
+    };
+    if (e == cudaSuccess) e = save(true);
+    const bool had_cfg = s->has_cfg;
+    const LaunchCfg old_cfg = s->cfg;
+    LaunchCfg best = cand[0];
+    float best_ms = 1e30f;
+    for (size_t ci = 0; ci < cand.size() && e == cudaSuccess; ++ci) {
+        s->cfg = cand[ci];
+        s->has_cfg = true;
+        float times[3];
+        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // first run warms up
+            e = save(false);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, cs);
+            if (e == cudaSuccess && launch_generate(s, tmp, count, 0, dtype, cs) != WN_OK) e = cudaErrorLaunchFailure;
+            if (e == cudaSuccess) e = cudaEventRecord(e1, cs);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) times[rep - 1] = ms;
+        }
+        if (e != cudaSuccess) break;
+        std::sort(times, times + 3);
+        if (times[1] < best_ms) {
+            best_ms = times[1];
+            best = cand[ci];
+        }
+    }
+    if (e == cudaSuccess) e = save(false);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    cleanup();
+    if (e != cudaSuccess) {
+        s->cfg = old_cfg;
+        s->has_cfg = had_cfg;
+        return cuda_fail("wn_autotune", e);
+    }
+    s->cfg = best;
+    s->has_cfg = true;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        cache[key] = best;
+    }
+    if (quads_per_thread) *quads_per_thread = (uint32_t)best.qt;
+    if (threads) *threads = best.threads;
     return WN_OK;
 }
 

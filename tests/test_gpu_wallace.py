@@ -273,4 +273,18 @@ def test_rejects_uncompiled_shape(wn):
     with pytest.raises(wn.WnError):
         wn.wn_set_config(h, 3, 512)
     wn.wn_set_config(h, 0, 0)
-    assert wn.wn_get_config(h) == (4, 256)
+    assert wn.wn_get_config(h) == (8, 128)
+
+
+def test_autotune_keeps_sequence_and_matches_oracle(wn, torch):
+    N, R, n, count = 4096, 2, 64, 3 * 4095 + 10
+    seeds = list(range(300, 300 + n))
+    h = wn.wn_create_streams([N] * n, [R] * n, seeds)
+    before = [wn.wn_get_state(h, i) for i in range(n)]
+    qt, th = wn.wn_autotune(h, count)
+    assert wn.wn_get_config(h) == (qt, th) and qt * th >= N // 4
+    assert [wn.wn_get_state(h, i) for i in range(n)] == before  # state restored
+    got = _gen(wn, torch, h, count).cpu().numpy().reshape(n, count)
+    for i in (0, n - 1):
+        ref = oracle.Stream(N, R, seeds[i]).generate(count)
+        assert_fp32_close(got[i], ref, passes_fresh(count, N, R), f"autotuned stream {i}")
