@@ -110,6 +110,23 @@ wn_status wn_generate_ex(void *out, uint64_t count, wn_stream *s, wn_dtype dtype
  */
 wn_status wn_generate_host(void *host_out, uint64_t count, wn_stream *s, wn_dtype dtype, void *cuda_stream);
 
+/*
+ * wn_gbm -- a fused Monte Carlo consumer: geometric Brownian motion terminal
+ * prices driven by the streams' own normals, which never leave the chip.
+ * Stream i serves paths [i*paths_per_stream, (i+1)*paths_per_stream); path p
+ * of stream i takes value j*paths_per_stream + p of the stream's sequence as
+ * its step-j normal Z_j and follows the exact log step
+ * S <- S exp((mu - sigma^2/2) dt + sigma sqrt(dt) Z_j) from S0 for `steps`
+ * steps.  ST_out (device, float, n_streams * paths_per_stream entries)
+ * receives the terminal prices.  Requires, for every stream, that
+ * paths_per_stream divide pool_N - 1, that steps * paths_per_stream be a
+ * multiple of pool_N - 1, and that no values of a partly returned block be
+ * pending (WN_EINVAL otherwise).  Advances each stream as generating
+ * steps * paths_per_stream values would.  Asynchronous on cuda_stream.
+ */
+wn_status wn_gbm(wn_stream *s, float *ST_out, uint32_t paths_per_stream, uint32_t steps, double S0, double mu,
+                 double sigma, double dt, void *cuda_stream);
+
 /* wn_set_cuda_stream -- CUDA stream used by wn_generate. */
 wn_status wn_set_cuda_stream(wn_stream *s, void *cuda_stream);
 

@@ -24,7 +24,7 @@ __all__ = [
     "WN_F32", "WN_BF16", "WN_F16", "WnError",
     "wn_create", "wn_create_streams", "wn_destroy", "wn_generate", "wn_generate_ex",
     "wn_generate_host",
-    "wn_set_cuda_stream", "wn_set_config", "wn_get_config", "wn_autotune", "wn_num_streams", "wn_get_pool", "wn_get_state",
+    "wn_set_cuda_stream", "wn_set_config", "wn_get_config", "wn_autotune", "wn_gbm", "wn_num_streams", "wn_get_pool", "wn_get_state",
     "wn_rng_draws", "wn_boxmuller", "wn_last_error", "library_path", "load",
 ]
 
@@ -60,6 +60,8 @@ def _load() -> ctypes.CDLL:
         "wn_set_config": (_i, [_p, _u32, _u32]),
         "wn_get_config": (_i, [_p, _p, _p]),
         "wn_autotune": (_i, [_p, _u64, _i, _p, _p, _p]),
+        "wn_gbm": (_i, [_p, _p, _u32, _u32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                        ctypes.c_double, _p]),
         "wn_num_streams": (_u32, [_p]),
         "wn_get_pool": (_i, [_p, _u32, _p]),
         "wn_get_state": (_i, [_p, _u32, _p, _p, _p, _p, _p]),
@@ -222,6 +224,14 @@ def wn_autotune(h: Handle, count: int, dtype: int = WN_F32, cuda_stream=None) ->
     _check(_L().wn_autotune(h.ptr, count, dtype, _stream_ptr(cuda_stream), ctypes.addressof(q),
                             ctypes.addressof(t)), "wn_autotune")
     return q.value, t.value
+
+
+def wn_gbm(st_out, h: Handle, paths_per_stream: int, steps: int, S0: float, mu: float, sigma: float,
+           dt: float, cuda_stream=None) -> None:
+    """st_out: float32 CUDA tensor of h.n * paths_per_stream terminal prices."""
+    ptr = _out_ptr(st_out, h.n * paths_per_stream, WN_F32)
+    _check(_L().wn_gbm(h.ptr, ptr, paths_per_stream, steps, S0, mu, sigma, dt, _stream_ptr(cuda_stream)),
+           "wn_gbm")
 
 
 def wn_num_streams(h: Handle) -> int:

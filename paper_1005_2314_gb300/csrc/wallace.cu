@@ -3,6 +3,7 @@
 // the stream initialisation kernel.  The generate kernel itself is in
 // wn_gen.cuh (instantiated per output type in gen_*.cu).
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -99,6 +100,9 @@ struct wn_stream {
     size_t stage_bytes = 0;
     cudaStream_t copy_cs = nullptr;
     cudaEvent_t ev_gen[2] = {nullptr, nullptr}, ev_copy[2] = {nullptr, nullptr};
+    // values of each stream's last block already returned, as of the calls
+    // enqueued so far (N-1: at a block boundary)
+    std::vector<uint32_t> k_host;
     // window address where dynamic shared memory starts (probed at creation)
     uint32_t smem_base = 0;
     bool uniform_N = true;  // every stream has pool n_max
@@ -190,6 +194,21 @@ wn_status launch_generate(wn_stream *s, void *out, uint64_t count, uint32_t warm
     return WN_OK;
 }
 
+// Host mirror of each stream's position within its current block after
+// `count` more values (the device state advances the same way).
+void advance_k(wn_stream *s, uint64_t count)
+{
+    for (uint32_t i = 0; i < s->n; ++i) {
+        const uint64_t per = s->N[i] - 1, left = per - s->k_host[i];
+        if (count <= left) {
+            s->k_host[i] += (uint32_t)count;
+        } else {
+            const uint64_t tail = (count - left) % per;
+            s->k_host[i] = tail == 0 ? (uint32_t)per : (uint32_t)tail;
+        }
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -207,6 +226,8 @@ wn_stream *wn_create_streams(uint32_t n_streams, const uint32_t *pool_N, const u
     wn_stream *s = new wn_stream();
     s->n = n_streams;
     s->N.assign(pool_N, pool_N + n_streams);
+    s->k_host.resize(n_streams);
+    for (uint32_t i = 0; i < n_streams; ++i) s->k_host[i] = pool_N[i] - 1;
     s->R.assign(passes_R, passes_R + n_streams);
     std::vector<wn::StreamHdr> h(n_streams);
     uint64_t off = 0;
@@ -464,7 +485,9 @@ wn_status wn_generate_ex(void *out, uint64_t count, wn_stream *s, wn_dtype dtype
     if (count == 0) return WN_OK;
     if (!out) return fail(WN_EINVAL, "wn_generate: NULL output");
     if (reinterpret_cast<uintptr_t>(out) % 16 != 0) return fail(WN_EINVAL, "wn_generate: output not 16-byte aligned");
-    return launch_generate(s, out, count, 0, dtype, reinterpret_cast<cudaStream_t>(cuda_stream));
+    const wn_status st = launch_generate(s, out, count, 0, dtype, reinterpret_cast<cudaStream_t>(cuda_stream));
+    if (st == WN_OK) advance_k(s, count);
+    return st;
 }
 
 wn_status wn_generate_host(void *host_out, uint64_t count, wn_stream *s, wn_dtype dtype, void *cuda_stream)
@@ -498,6 +521,7 @@ wn_status wn_generate_host(void *host_out, uint64_t count, wn_stream *s, wn_dtyp
         if (j >= 2) WN_CU(cudaStreamWaitEvent(cs, s->ev_copy[b], 0));
         wn_status st = launch_generate(s, s->d_stage[b], c, 0, dtype, cs);
         if (st != WN_OK) return st;
+        advance_k(s, c);
         WN_CU(cudaEventRecord(s->ev_gen[b], cs));
         WN_CU(cudaStreamWaitEvent(s->copy_cs, s->ev_gen[b], 0));
         WN_CU(cudaMemcpy2DAsync(dst + done * esize, count * esize, s->d_stage[b], c * esize, c * esize, s->n,
@@ -507,6 +531,50 @@ wn_status wn_generate_host(void *host_out, uint64_t count, wn_stream *s, wn_dtyp
     }
     // later work on cuda_stream (and its synchronisation) follows the copies
     for (int b = 0; b < 2; ++b) WN_CU(cudaStreamWaitEvent(cs, s->ev_copy[b], 0));
+    return WN_OK;
+}
+
+wn_status wn_gbm(wn_stream *s, float *ST_out, uint32_t paths_per_stream, uint32_t steps, double S0, double mu,
+                 double sigma, double dt, void *cuda_stream)
+{
+    if (!s) return fail(WN_EINVAL, "wn_gbm: NULL handle");
+    if (!ST_out || paths_per_stream == 0 || steps == 0 || !(S0 > 0.0) || !(sigma >= 0.0) || !(dt > 0.0))
+        return fail(WN_EINVAL, "wn_gbm: NULL output or non-positive paths, steps, S0, dt, or negative sigma");
+    for (uint32_t i = 0; i < s->n; ++i) {
+        const uint32_t per = s->N[i] - 1;
+        if (per % paths_per_stream != 0 || ((uint64_t)steps * paths_per_stream) % per != 0)
+            return fail(WN_EINVAL, "wn_gbm: paths_per_stream must divide pool_N-1 and steps*paths_per_stream "
+                                   "must be a multiple of pool_N-1 for every stream");
+        if (s->k_host[i] != per)
+            return fail(WN_EINVAL, "wn_gbm: stream " + std::to_string(i) +
+                                       " has values of a partly returned block pending");
+    }
+    wn::GenArgs a;
+    a.hdr = s->d_hdr;
+    a.pools = s->d_pools;
+    a.out = nullptr;
+    a.count = (uint64_t)steps * paths_per_stream;
+    a.out_stride = 0;
+    a.n_streams = s->n;
+    a.n_max = s->n_max;
+    a.r_max = s->r_max;
+    a.warmup_blocks = 0;
+    wn::GbmArgs g;
+    g.st = ST_out;
+    g.ppg = paths_per_stream;
+    g.S0 = (float)S0;
+    g.drift_total = (float)((double)steps * (mu - 0.5 * sigma * sigma) * dt);
+    g.vol = (float)(sigma * std::sqrt(dt));
+    const uint32_t nq = s->n_max / 4;
+    LaunchCfg c;
+    if (nq <= 128) c = {1, 1024, std::max(32u, (nq + 31u) / 32u * 32u)};
+    else if (nq <= 1024) c = {4, 288, nq / 4};
+    else c = {8, 544, nq / 8};
+    const bool full = s->uniform_N && (uint64_t)c.threads * c.qt == nq;
+    const size_t smem = wn::gen_smem_bytes(s->smem_base, s->n_max, s->r_max);
+    const cudaError_t e = wn::launch_gbm(a, g, c, full, smem, reinterpret_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail("wn_gbm launch", e);
+    advance_k(s, a.count);
     return WN_OK;
 }
 

@@ -215,7 +215,22 @@ __device__ __forceinline__ void store4(__half *p, float a, float b, float c, flo
     *reinterpret_cast<uint2 *>(p) = u;
 }
 
-enum { EMIT_NONE = 0, EMIT_WHOLE = 1, EMIT_PART = 2 };
+enum { EMIT_NONE = 0, EMIT_WHOLE = 1, EMIT_PART = 2, EMIT_GBM = 3 };
+
+// Fused Monte Carlo consumer (geometric Brownian motion): the stream's values
+// drive paths and never leave the chip.  Path p of a stream takes value
+// j ppg + p as its step-j normal; ppg divides N-1, so pool position i of
+// every block feeds path i mod ppg.  A compute thread therefore keeps one
+// running sum of the (scaled) values per pool position it owns, in
+// registers; at the end the k = (N-1)/ppg sums of each path are added and
+// S_T = S0 exp(steps (mu - sigma^2/2) dt + sigma sqrt(dt) sum).
+struct GbmArgs {
+    float *st;          // terminal prices: stream i writes st[i ppg .. i ppg + ppg)
+    uint32_t ppg;       // paths per stream
+    float S0;           // initial price
+    float drift_total;  // steps (mu - sigma^2/2) dt
+    float vol;          // sigma sqrt(dt)
+};
 
 // One pass over this thread's quadruples q = q0 + 32 j (j < QT): gather from
 // the buffer at window address rd, store the four results contiguously into
@@ -236,12 +251,14 @@ enum { EMIT_NONE = 0, EMIT_WHOLE = 1, EMIT_PART = 2 };
 //    (predecessor in another warp) and last one (successor in another warp,
 //    or the reserved slot) use single stores;
 //  * EMIT_PART: the first n values of a partial last block, single stores.
+//  * EMIT_GBM: add the scaled values to the per-position sums `acc`.
 // SYNC (one pass per block) puts a barrier between the arithmetic and the
 // stores so that the control warp's scale for this block is visible.
 template <int QT, bool FINAL, bool FULL, int EMIT, int A, typename OutT>
 __device__ __forceinline__ void pass_quads(uint32_t rd, uint32_t wr, uint32_t tab, uint32_t q0, uint32_t lane,
                                            uint32_t m4, uint32_t half, uint32_t nq, float2 &part, bool sync,
-                                           OutT *__restrict__ ob, const float *sc_ptr, uint32_t n)
+                                           OutT *__restrict__ ob, const float *sc_ptr, uint32_t n,
+                                           float2 (&acc)[QT][2])
 {
     const uint4 P = lds4u(tab);
     const float4 sg = lds4(tab + 16u + 16u * (lane & 15u));
@@ -281,6 +298,14 @@ __device__ __forceinline__ void pass_quads(uint32_t rd, uint32_t wr, uint32_t ta
     if (sync) __syncthreads();
     const float sc = *sc_ptr;
     const float2 sc2 = make_float2(sc, sc);
+    if (EMIT == EMIT_GBM) {
+#pragma unroll
+        for (int j = 0; j < QT; ++j) {
+            acc[j][0] = ffma2(y[j][0], sc2, acc[j][0]);
+            acc[j][1] = ffma2(y[j][1], sc2, acc[j][1]);
+        }
+        return;
+    }
     const uint32_t src = (lane + 31u) & 31u;
     const bool l31 = (lane == 31u);
     float l1 = 0.f, l2 = 0.f, l3 = 0.f;  // this thread's values 1..3 of the previous j
@@ -354,10 +379,10 @@ __device__ __forceinline__ void pass_quads(uint32_t rd, uint32_t wr, uint32_t ta
 // pass per block the final pass is also the first, so it waits for the scale
 // at a mid-phase barrier.
 // ---------------------------------------------------------------------------
-template <int QT, bool FULL, typename OutT>
+template <int QT, bool FULL, typename OutT, bool GBM>
 __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__restrict__ pool_g,
                                            OutT *__restrict__ out, uint64_t out_off, uint64_t count,
-                                           bool store, uint32_t n_max, uint32_t r_max)
+                                           bool store, uint32_t n_max, uint32_t r_max, const GbmArgs &gbm)
 {
     unsigned char *smem = wn_smem;
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
@@ -439,6 +464,9 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
     uint32_t a = (uint32_t)((out_off + n0) & 3u);  // alignment of ob within 16 bytes
     uint32_t cb = 0;                               // buffer (0 or 1) holding the current pool
     const bool one_pass = (R == 1);
+    float2 acc[QT][2];  // GBM: running sums of this thread's pool positions
+#pragma unroll
+    for (int j = 0; j < QT; ++j) acc[j][0] = acc[j][1] = make_float2(0.f, 0.f);
     for (uint64_t b = 0; b < nb; ++b) {
         const uint32_t tb = tabs_s + (uint32_t)(b & 1) * r_max * (uint32_t)sizeof(PassTab);
         for (uint32_t p = 0; p < R; ++p) {
@@ -457,35 +485,38 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
             } else if (p + 1 < R) {
                 float2 part;
                 pass_quads<QT, false, FULL, EMIT_NONE, 0, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part, false,
-                                                               nullptr, nullptr, 0);
+                                                               nullptr, nullptr, 0, acc);
             } else {
                 float2 part = make_float2(0.f, 0.f);
                 const float *scp = &ctl->sc[b & 1];
                 const bool whole = (b + 1 < nb) || tail == 0;
-                if (!store) {
+                if (GBM) {
+                    pass_quads<QT, true, FULL, EMIT_GBM, 0, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part,
+                                                                 one_pass, ob, scp, 0, acc);
+                } else if (!store) {
                     pass_quads<QT, true, FULL, EMIT_NONE, 0, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                  false, ob, scp, 0);
+                                                                  false, ob, scp, 0, acc);
                     if (one_pass) __syncthreads();
                 } else if (!whole) {
                     pass_quads<QT, true, FULL, EMIT_PART, 0, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                  one_pass, ob, scp, (uint32_t)tail);
+                                                                  one_pass, ob, scp, (uint32_t)tail, acc);
                 } else {
                     switch (a) {
                     case 0:
                         pass_quads<QT, true, FULL, EMIT_WHOLE, 0, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                       one_pass, ob, scp, 0);
+                                                                       one_pass, ob, scp, 0, acc);
                         break;
                     case 1:
                         pass_quads<QT, true, FULL, EMIT_WHOLE, 1, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                       one_pass, ob, scp, 0);
+                                                                       one_pass, ob, scp, 0, acc);
                         break;
                     case 2:
                         pass_quads<QT, true, FULL, EMIT_WHOLE, 2, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                       one_pass, ob, scp, 0);
+                                                                       one_pass, ob, scp, 0, acc);
                         break;
                     default:
                         pass_quads<QT, true, FULL, EMIT_WHOLE, 3, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                       one_pass, ob, scp, 0);
+                                                                       one_pass, ob, scp, 0, acc);
                         break;
                     }
                 }
@@ -519,6 +550,25 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
     } else if (tid == 0 && nb == 0) {
         h->k = k0 + (uint32_t)n0;
     }
+    if (GBM) {
+        // per-position sums into the buffer that does not hold the pool, then
+        // each path adds its k = (N-1)/ppg positions
+        const uint32_t accb = W0 + (cb ^ 1u) * bsz;
+        if (!control) {
+#pragma unroll
+            for (int j = 0; j < QT; ++j) {
+                const uint32_t q = q0 + 32u * j;
+                if (FULL || q < nq) sts4(accb + 16u * q, acc[j][0], acc[j][1]);
+            }
+        }
+        __syncthreads();
+        const uint32_t k = (N - 1) / gbm.ppg;
+        for (uint32_t p = tid; p < gbm.ppg; p += blockDim.x) {
+            float tot = 0.f;
+            for (uint32_t m = 0; m < k; ++m) tot += lds(accb + 4u * (p + m * gbm.ppg));
+            gbm.st[(uint64_t)blockIdx.x * gbm.ppg + p] = gbm.S0 * expf(fmaf(gbm.vol, tot, gbm.drift_total));
+        }
+    }
 }
 
 // FULL: every stream of the launch has exactly (blockDim.x - 32) * QT
@@ -531,8 +581,29 @@ __global__ void __launch_bounds__(MAXT, MINB) generate_kernel(GenArgs a)
     const uint64_t count = a.warmup_blocks ? (uint64_t)a.warmup_blocks * (N - 1) : a.count;
     const uint64_t off = (uint64_t)blockIdx.x * a.out_stride;
     OutT *out = a.out ? reinterpret_cast<OutT *>(a.out) + off : nullptr;
-    run_stream<QT, FULL, OutT>(h, a.pools + h->pool_off, out, off, count, a.warmup_blocks == 0, a.n_max, a.r_max);
+    const GbmArgs none{};
+    run_stream<QT, FULL, OutT, false>(h, a.pools + h->pool_off, out, off, count, a.warmup_blocks == 0, a.n_max,
+                                      a.r_max, none);
 }
+
+// The fused GBM consumer: every stream of the launch returns steps * ppg
+// values (a whole number of blocks, starting at a block boundary) into path
+// sums instead of memory.
+template <int QT, int MAXT, int MINB, bool FULL>
+__global__ void __launch_bounds__(MAXT, MINB) gbm_kernel(GenArgs a, GbmArgs g)
+{
+    StreamHdr *h = a.hdr + blockIdx.x;
+    run_stream<QT, FULL, float, true>(h, a.pools + h->pool_off, nullptr, 0, a.count, false, a.n_max, a.r_max, g);
+}
+
+// Shapes of the GBM consumer {quadruples per thread, thread bound, min CTAs
+// per SM}: fewer resident CTAs than generate's, since the per-position sums
+// take another 4 QT registers per thread.
+constexpr int kGbmShapes[][3] = {{1, 1024, 1}, {4, 288, 3}, {8, 544, 1}};
+
+// Launch of the GBM consumer (defined in gen_f32.cu).
+cudaError_t launch_gbm(const GenArgs &a, const GbmArgs &g, const LaunchCfg &c, bool full, size_t smem,
+                       cudaStream_t cs);
 
 template <int QT, int MAXT, int MINB, typename OutT>
 cudaError_t launch_shape(const GenArgs &a, uint32_t threads, bool full, size_t smem, cudaStream_t cs)
