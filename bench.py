@@ -323,6 +323,41 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": None, "unit": "variates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
                "error": str(ex)[:200]}
 
+    # the batched uneven-request workload: 10,000 streams, pool from
+    # {1024, 4096, 16384}, R from {1, 2, 4}, log-uniform lengths 2^10..2^24,
+    # FP32 packed contiguously; one captured graph of persistent kernels
+    batched = None
+    if not args.no_batch:
+        from paper_1005_2314_gb300.workloads import packed_offsets, uneven_batch
+        bN, bR, bc = uneven_batch(10000, seed=12345)
+        boff = packed_offsets(bc)
+        btotal = int(bc.sum())
+        del out, bm_out
+        bout = torch.empty(btotal, dtype=torch.float32, device=dev)
+        hb = wn.wn_create_streams(bN, bR, [rank * 10000 + i + 1 for i in range(10000)], WARMUP_BLOCKS, stream)
+        wn.wn_autotune_batch(bout, bc, boff, hb, wn.WN_F32, stream)
+        wn.wn_generate_batch(bout, bc, boff, hb, wn.WN_F32, True, stream)  # captures the graph
+        torch.cuda.synchronize()
+        bms = []
+        for i in range(3):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            wn.wn_generate_batch(bout, bc, boff, hb, wn.WN_F32, True, stream)  # graph replay
+            b.record(stream)
+            bms.append((a, b))
+        torch.cuda.synchronize()
+        bt = sorted(x.elapsed_time(y) for x, y in bms)[1]
+        batched = {"value": btotal / (bt / 1e3), "unit": "variates/s", "ms_per_replay": bt,
+                   "variates_per_replay": btotal, "streams": 10000,
+                   "achieved_gbs": round(btotal * 4 / (bt / 1e3) / 1e9, 1),
+                   "longest_request": int(bc.max()),
+                   "how": "wn_generate_batch with use_graph: per pool size one persistent kernel (atomic claim, "
+                          "longest request first), groups forked on branch streams, captured once and replayed; "
+                          "launch shapes from wn_autotune_batch; median of 3 replays"}
+        wn.wn_destroy(hb)
+        del bout
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = _cpu_cores()
@@ -340,6 +375,7 @@ def run_ours(args, rank, world, local_rank):
             "comparison": {"boxmuller_philox4x32_10": {"value": bm_value, "unit": "variates/s",
                                                        "ms_per_step": bm_step,
                                                        "wallace_over_boxmuller": value / world / bm_value}},
+            "batched_uneven": batched,
             "create_s": create_s,
             "context": {"torch_fill_write_gbs": round(fill_gbs, 1),
                         "frac_of_fill": round(achieved / fill_gbs, 4)}}
@@ -375,6 +411,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-request leg")
     ap.add_argument("--streams", type=int, default=STREAMS, help="streams per GPU (default 4096)")
     ap.add_argument("--per-stream", type=int, default=PER_STREAM, help="values per stream per step")
     ap.add_argument("--shape", default="",

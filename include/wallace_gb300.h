@@ -111,6 +111,34 @@ wn_status wn_generate_ex(void *out, uint64_t count, wn_stream *s, wn_dtype dtype
 wn_status wn_generate_host(void *host_out, uint64_t count, wn_stream *s, wn_dtype dtype, void *cuda_stream);
 
 /*
+ * wn_generate_batch -- uneven requests in one call: stream i of `s` returns
+ * its next counts[i] values (0 allowed) as `dtype` to out + offsets[i]
+ * elements (host arrays of wn_num_streams(s) entries; `out` 16-byte aligned;
+ * the ranges must not overlap).  Streams are grouped by pool size; each group
+ * runs as one persistent kernel whose CTAs claim streams, longest request
+ * first, from an atomic counter in device memory the handle owns, and the
+ * groups run concurrently on branch streams joined back into cuda_stream.
+ * use_graph != 0: the counter reset and the group launches are captured once
+ * into a CUDA graph kept by the handle, and later calls with the same out,
+ * counts, offsets and dtype replay it (a call with other arguments captures
+ * anew).  Streams continue their sequences as with wn_generate.
+ * Asynchronous on cuda_stream.
+ */
+wn_status wn_generate_batch(void *out, const uint64_t *counts, const uint64_t *offsets, wn_stream *s,
+                            wn_dtype dtype, int use_graph, void *cuda_stream);
+
+/*
+ * wn_autotune_batch -- picks, for each pool size of the batch described by
+ * out/counts/offsets/dtype (as in wn_generate_batch), the compiled launch
+ * shape whose persistent kernel serves that group fastest, timing each on a
+ * saved copy of the state (the streams' sequences are unaffected; `out` is
+ * overwritten with scratch values).  Later wn_generate_batch calls use the
+ * chosen shapes.  Synchronous.
+ */
+wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *offsets, wn_stream *s,
+                            wn_dtype dtype, void *cuda_stream);
+
+/*
  * wn_gbm -- a fused Monte Carlo consumer: geometric Brownian motion terminal
  * prices driven by the streams' own normals, which never leave the chip.
  * Stream i serves paths [i*paths_per_stream, (i+1)*paths_per_stream); path p

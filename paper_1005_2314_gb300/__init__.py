@@ -24,7 +24,8 @@ __all__ = [
     "WN_F32", "WN_BF16", "WN_F16", "WnError",
     "wn_create", "wn_create_streams", "wn_destroy", "wn_generate", "wn_generate_ex",
     "wn_generate_host",
-    "wn_set_cuda_stream", "wn_set_config", "wn_get_config", "wn_autotune", "wn_gbm", "wn_num_streams", "wn_get_pool", "wn_get_state",
+    "wn_set_cuda_stream", "wn_set_config", "wn_get_config", "wn_autotune", "wn_gbm", "wn_generate_batch",
+    "wn_autotune_batch", "wn_num_streams", "wn_get_pool", "wn_get_state",
     "wn_rng_draws", "wn_boxmuller", "wn_last_error", "library_path", "load",
 ]
 
@@ -60,6 +61,8 @@ def _load() -> ctypes.CDLL:
         "wn_set_config": (_i, [_p, _u32, _u32]),
         "wn_get_config": (_i, [_p, _p, _p]),
         "wn_autotune": (_i, [_p, _u64, _i, _p, _p, _p]),
+        "wn_generate_batch": (_i, [_p, _p, _p, _p, _i, _i, _p]),
+        "wn_autotune_batch": (_i, [_p, _p, _p, _p, _i, _p]),
         "wn_gbm": (_i, [_p, _p, _u32, _u32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                         ctypes.c_double, _p]),
         "wn_num_streams": (_u32, [_p]),
@@ -224,6 +227,29 @@ def wn_autotune(h: Handle, count: int, dtype: int = WN_F32, cuda_stream=None) ->
     _check(_L().wn_autotune(h.ptr, count, dtype, _stream_ptr(cuda_stream), ctypes.addressof(q),
                             ctypes.addressof(t)), "wn_autotune")
     return q.value, t.value
+
+
+def _batch_arrays(h: Handle, counts, offsets):
+    counts = np.ascontiguousarray(np.asarray(counts, dtype=np.uint64))
+    offsets = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64))
+    if counts.shape != (h.n,) or offsets.shape != (h.n,):
+        raise ValueError(f"counts and offsets need {h.n} entries")
+    need = int(np.max(offsets + counts)) if h.n else 0
+    return counts, offsets, need
+
+
+def wn_generate_batch(out, counts, offsets, h: Handle, dtype: int = WN_F32, use_graph: bool = False,
+                      cuda_stream=None) -> None:
+    """Stream i's next counts[i] values go to out[offsets[i]:offsets[i]+counts[i]]."""
+    counts, offsets, need = _batch_arrays(h, counts, offsets)
+    _check(_L().wn_generate_batch(_out_ptr(out, need, dtype), counts.ctypes.data, offsets.ctypes.data, h.ptr,
+                                  dtype, int(bool(use_graph)), _stream_ptr(cuda_stream)), "wn_generate_batch")
+
+
+def wn_autotune_batch(out, counts, offsets, h: Handle, dtype: int = WN_F32, cuda_stream=None) -> None:
+    counts, offsets, need = _batch_arrays(h, counts, offsets)
+    _check(_L().wn_autotune_batch(_out_ptr(out, need, dtype), counts.ctypes.data, offsets.ctypes.data, h.ptr,
+                                  dtype, _stream_ptr(cuda_stream)), "wn_autotune_batch")
 
 
 def wn_gbm(st_out, h: Handle, paths_per_stream: int, steps: int, S0: float, mu: float, sigma: float,

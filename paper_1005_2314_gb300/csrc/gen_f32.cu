@@ -8,6 +8,12 @@ cudaError_t launch_generate_f32(const GenArgs &a, const LaunchCfg &c, bool full,
     return launch_generate_t<float>(a, c, full, smem, cs);
 }
 
+cudaError_t launch_persist_f32(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full, size_t smem,
+                               int sms, cudaStream_t cs)
+{
+    return launch_persist_t<float>(a, bq, c, full, smem, sms, cs);
+}
+
 template <int QT, int MAXT, int MINB>
 static cudaError_t launch_gbm_shape(const GenArgs &a, const GbmArgs &g, uint32_t threads, bool full, size_t smem,
                                     cudaStream_t cs)

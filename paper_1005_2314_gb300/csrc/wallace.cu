@@ -106,6 +106,20 @@ struct wn_stream {
     // window address where dynamic shared memory starts (probed at creation)
     uint32_t smem_base = 0;
     bool uniform_N = true;  // every stream has pool n_max
+    int sms = 0;  // multiprocessors of the device
+    // batches (wn_generate_batch): per-stream descriptors on the device, one
+    // claim counter per pool-size group, branch streams for the groups, the
+    // tuned shape per pool size, and the last captured graph
+    uint64_t *d_bcounts = nullptr, *d_boffsets = nullptr;
+    uint32_t *d_border = nullptr, *d_queue = nullptr;
+    std::vector<cudaStream_t> branch;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    std::map<uint32_t, wn::LaunchCfg> group_cfg;
+    cudaGraphExec_t gexec = nullptr;
+    void *g_out = nullptr;
+    int g_dtype = -1;
+    std::vector<uint64_t> g_counts, g_offsets;
     // launch configuration chosen by wn_set_config (otherwise the default)
     bool has_cfg = false;
     wn::LaunchCfg cfg{};
@@ -209,6 +223,127 @@ void advance_k(wn_stream *s, uint64_t count)
     }
 }
 
+// The same for stream i alone.
+void advance_k_one(wn_stream *s, uint32_t i, uint64_t count)
+{
+    const uint64_t per = s->N[i] - 1, left = per - s->k_host[i];
+    if (count <= left) {
+        s->k_host[i] += (uint32_t)count;
+    } else {
+        const uint64_t tail = (count - left) % per;
+        s->k_host[i] = tail == 0 ? (uint32_t)per : (uint32_t)tail;
+    }
+}
+
+// One pool-size group of a batch: its streams occupy order[start, start+len).
+struct Group {
+    uint32_t N = 0, r_max = 0, start = 0, len = 0;
+};
+
+// Groups streams by pool size and orders each group longest first (cost
+// counts[i] (R_i + 1): a block costs R passes plus its stores).
+std::vector<Group> plan_batch(const wn_stream *s, const uint64_t *counts, std::vector<uint32_t> &order)
+{
+    std::map<uint32_t, std::vector<uint32_t>> by_n;
+    for (uint32_t i = 0; i < s->n; ++i) by_n[s->N[i]].push_back(i);
+    std::vector<Group> groups;
+    order.clear();
+    for (auto &kv : by_n) {
+        auto &v = kv.second;
+        std::stable_sort(v.begin(), v.end(), [&](uint32_t x, uint32_t y) {
+            return counts[x] * (s->R[x] + 1ull) > counts[y] * (s->R[y] + 1ull);
+        });
+        Group g;
+        g.N = kv.first;
+        g.start = (uint32_t)order.size();
+        g.len = (uint32_t)v.size();
+        for (uint32_t i : v) g.r_max = std::max(g.r_max, s->R[i]);
+        order.insert(order.end(), v.begin(), v.end());
+        groups.push_back(g);
+    }
+    return groups;
+}
+
+wn_status ensure_batch_buffers(wn_stream *s, size_t n_groups)
+{
+    if (!s->d_bcounts) {
+        WN_CU(cudaMalloc(&s->d_bcounts, sizeof(uint64_t) * s->n));
+        WN_CU(cudaMalloc(&s->d_boffsets, sizeof(uint64_t) * s->n));
+        WN_CU(cudaMalloc(&s->d_border, sizeof(uint32_t) * s->n));
+        WN_CU(cudaMalloc(&s->d_queue, sizeof(uint32_t) * 16));
+        WN_CU(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming));
+    }
+    while (s->branch.size() < n_groups) {
+        cudaStream_t b;
+        cudaEvent_t j;
+        WN_CU(cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking));
+        WN_CU(cudaEventCreateWithFlags(&j, cudaEventDisableTiming));
+        s->branch.push_back(b);
+        s->join.push_back(j);
+    }
+    return WN_OK;
+}
+
+LaunchCfg group_cfg(const wn_stream *s, uint32_t N)
+{
+    auto it = s->group_cfg.find(N);
+    return it != s->group_cfg.end() ? it->second : pick_cfg(N);
+}
+
+// Enqueues a batch whose descriptors are already on the device: reset the
+// claim counters, fork one branch per group, launch each group's persistent
+// kernel, join.
+wn_status enqueue_batch(wn_stream *s, const std::vector<Group> &groups, void *out, wn_dtype dt, cudaStream_t cs)
+{
+    WN_CU(cudaMemsetAsync(s->d_queue, 0, sizeof(uint32_t) * 16, cs));
+    WN_CU(cudaEventRecord(s->fork, cs));
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        const Group &g = groups[gi];
+        cudaStream_t b = s->branch[gi];
+        WN_CU(cudaStreamWaitEvent(b, s->fork, 0));
+        wn::GenArgs a;
+        a.hdr = s->d_hdr;
+        a.pools = s->d_pools;
+        a.out = out;
+        a.count = 0;
+        a.out_stride = 0;
+        a.n_streams = g.len;
+        a.n_max = g.N;
+        a.r_max = g.r_max;
+        a.warmup_blocks = 0;
+        wn::BatchArgs bq;
+        bq.order = s->d_border + g.start;
+        bq.offsets = s->d_boffsets;
+        bq.counts = s->d_bcounts;
+        bq.n_items = g.len;
+        bq.queue = s->d_queue + gi;
+        const LaunchCfg c = group_cfg(s, g.N);
+        const bool full = (uint64_t)c.threads * c.qt == g.N / 4;
+        const size_t smem = wn::gen_smem_bytes(s->smem_base, g.N, g.r_max);
+        cudaError_t e;
+        switch (dt) {
+        case WN_F32: e = wn::launch_persist_f32(a, bq, c, full, smem, s->sms, b); break;
+        case WN_BF16: e = wn::launch_persist_bf16(a, bq, c, full, smem, s->sms, b); break;
+        default: e = wn::launch_persist_f16(a, bq, c, full, smem, s->sms, b); break;
+        }
+        if (e != cudaSuccess) return cuda_fail("wn_generate_batch: launch", e);
+        WN_CU(cudaEventRecord(s->join[gi], b));
+        WN_CU(cudaStreamWaitEvent(cs, s->join[gi], 0));
+    }
+    return WN_OK;
+}
+
+wn_status check_batch_args(const wn_stream *s, const void *out, const uint64_t *counts, const uint64_t *offsets,
+                           wn_dtype dtype)
+{
+    if (!s) return fail(WN_EINVAL, "wn_generate_batch: NULL handle");
+    if (dtype != WN_F32 && dtype != WN_BF16 && dtype != WN_F16) return fail(WN_EINVAL, "wn_generate_batch: unknown dtype");
+    if (!counts || !offsets) return fail(WN_EINVAL, "wn_generate_batch: NULL counts or offsets");
+    if (!out || reinterpret_cast<uintptr_t>(out) % 16 != 0)
+        return fail(WN_EINVAL, "wn_generate_batch: output NULL or not 16-byte aligned");
+    return WN_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -250,6 +385,7 @@ wn_stream *wn_create_streams(uint32_t n_streams, const uint32_t *pool_N, const u
     }
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_hdr, sizeof(wn::StreamHdr) * n_streams);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_pools, sizeof(float) * off);
     if (e != cudaSuccess) {
@@ -323,6 +459,14 @@ void wn_destroy(wn_stream *s)
         if (s->ev_copy[b]) cudaEventDestroy(s->ev_copy[b]);
     }
     if (s->copy_cs) cudaStreamDestroy(s->copy_cs);
+    if (s->d_bcounts) cudaFree(s->d_bcounts);
+    if (s->d_boffsets) cudaFree(s->d_boffsets);
+    if (s->d_border) cudaFree(s->d_border);
+    if (s->d_queue) cudaFree(s->d_queue);
+    for (auto b : s->branch) cudaStreamDestroy(b);
+    for (auto j : s->join) cudaEventDestroy(j);
+    if (s->fork) cudaEventDestroy(s->fork);
+    if (s->gexec) cudaGraphExecDestroy(s->gexec);
     delete s;
 }
 
@@ -531,6 +675,145 @@ wn_status wn_generate_host(void *host_out, uint64_t count, wn_stream *s, wn_dtyp
     }
     // later work on cuda_stream (and its synchronisation) follows the copies
     for (int b = 0; b < 2; ++b) WN_CU(cudaStreamWaitEvent(cs, s->ev_copy[b], 0));
+    return WN_OK;
+}
+
+wn_status wn_generate_batch(void *out, const uint64_t *counts, const uint64_t *offsets, wn_stream *s, wn_dtype dtype,
+                            int use_graph, void *cuda_stream)
+{
+    wn_status st = check_batch_args(s, out, counts, offsets, dtype);
+    if (st != WN_OK) return st;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(cuda_stream);
+    std::vector<uint32_t> order;
+    const std::vector<Group> groups = plan_batch(s, counts, order);
+    if (groups.size() > 16) return fail(WN_EINVAL, "wn_generate_batch: more than 16 pool sizes");
+    if ((st = ensure_batch_buffers(s, groups.size())) != WN_OK) return st;
+    const bool same = use_graph && s->gexec && s->g_out == out && s->g_dtype == (int)dtype &&
+                      std::equal(counts, counts + s->n, s->g_counts.begin()) &&
+                      std::equal(offsets, offsets + s->n, s->g_offsets.begin());
+    if (!same) {
+        WN_CU(cudaMemcpyAsync(s->d_bcounts, counts, sizeof(uint64_t) * s->n, cudaMemcpyHostToDevice, cs));
+        WN_CU(cudaMemcpyAsync(s->d_boffsets, offsets, sizeof(uint64_t) * s->n, cudaMemcpyHostToDevice, cs));
+        WN_CU(cudaMemcpyAsync(s->d_border, order.data(), sizeof(uint32_t) * s->n, cudaMemcpyHostToDevice, cs));
+    }
+    if (!use_graph) {
+        if ((st = enqueue_batch(s, groups, out, dtype, cs)) != WN_OK) return st;
+    } else {
+        if (!same) {
+            // capture the counters' reset and the groups' launches once; the
+            // descriptors they read were uploaded above, in stream order
+            if (s->gexec) {
+                cudaGraphExecDestroy(s->gexec);
+                s->gexec = nullptr;
+            }
+            cudaStream_t cap = nullptr;
+            WN_CU(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                st = enqueue_batch(s, groups, out, dtype, cap);
+                e = cudaStreamEndCapture(cap, &graph);
+            }
+            if (e == cudaSuccess && st == WN_OK) e = cudaGraphInstantiate(&s->gexec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            cudaStreamDestroy(cap);
+            if (st != WN_OK) return st;
+            if (e != cudaSuccess) return cuda_fail("wn_generate_batch: graph capture", e);
+            s->g_out = out;
+            s->g_dtype = (int)dtype;
+            s->g_counts.assign(counts, counts + s->n);
+            s->g_offsets.assign(offsets, offsets + s->n);
+        }
+        WN_CU(cudaGraphLaunch(s->gexec, cs));
+    }
+    for (uint32_t i = 0; i < s->n; ++i) advance_k_one(s, i, counts[i]);
+    return WN_OK;
+}
+
+wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *offsets, wn_stream *s, wn_dtype dtype,
+                            void *cuda_stream)
+{
+    wn_status st = check_batch_args(s, out, counts, offsets, dtype);
+    if (st != WN_OK) return st;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(cuda_stream);
+    std::vector<uint32_t> order;
+    const std::vector<Group> groups = plan_batch(s, counts, order);
+    if (groups.size() > 16) return fail(WN_EINVAL, "wn_autotune_batch: more than 16 pool sizes");
+    if ((st = ensure_batch_buffers(s, groups.size())) != WN_OK) return st;
+    WN_CU(cudaMemcpyAsync(s->d_bcounts, counts, sizeof(uint64_t) * s->n, cudaMemcpyHostToDevice, cs));
+    WN_CU(cudaMemcpyAsync(s->d_boffsets, offsets, sizeof(uint64_t) * s->n, cudaMemcpyHostToDevice, cs));
+    WN_CU(cudaMemcpyAsync(s->d_border, order.data(), sizeof(uint32_t) * s->n, cudaMemcpyHostToDevice, cs));
+    size_t pool_floats = 0;
+    for (uint32_t i = 0; i < s->n; ++i) pool_floats += s->N[i];
+    wn::StreamHdr *hdr_bak = nullptr;
+    float *pool_bak = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&hdr_bak, sizeof(wn::StreamHdr) * s->n);
+    if (e == cudaSuccess) e = cudaMalloc(&pool_bak, sizeof(float) * pool_floats);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hdr_bak, s->d_hdr, sizeof(wn::StreamHdr) * s->n, cudaMemcpyDeviceToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pool_bak, s->d_pools, sizeof(float) * pool_floats, cudaMemcpyDeviceToDevice, cs);
+    auto restore = [&]() {
+        cudaError_t r = cudaMemcpyAsync(s->d_hdr, hdr_bak, sizeof(wn::StreamHdr) * s->n, cudaMemcpyDeviceToDevice, cs);
+        if (r == cudaSuccess)
+            r = cudaMemcpyAsync(s->d_pools, pool_bak, sizeof(float) * pool_floats, cudaMemcpyDeviceToDevice, cs);
+        return r;
+    };
+    std::map<uint32_t, LaunchCfg> chosen;
+    for (size_t gi = 0; gi < groups.size() && e == cudaSuccess; ++gi) {
+        const Group &g = groups[gi];
+        const uint32_t nq = g.N / 4;
+        float best_ms = 1e30f;
+        LaunchCfg best = pick_cfg(g.N);
+        for (const auto &k : wn::kShapes)
+            for (uint32_t t = 32; t + 32 <= (uint32_t)k[1] && e == cudaSuccess; t += 32) {
+                LaunchCfg c{k[0], k[1], t};
+                if (!cfg_ok(c, g.N) || (uint64_t)t * k[0] != nq) continue;  // full shapes only
+                s->group_cfg[g.N] = c;
+                std::vector<Group> one(1, g);
+                float times[2] = {0.f, 0.f};
+                for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+                    e = restore();
+                    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_queue, 0, sizeof(uint32_t) * 16, cs);
+                    if (e == cudaSuccess) e = cudaEventRecord(e0, cs);
+                    if (e == cudaSuccess) {
+                        const bool full = true;
+                        const size_t smem = wn::gen_smem_bytes(s->smem_base, g.N, g.r_max);
+                        wn::GenArgs a{s->d_hdr, s->d_pools, out, 0, 0, g.len, g.N, g.r_max, 0};
+                        wn::BatchArgs bq{s->d_border + g.start, s->d_boffsets, s->d_bcounts, g.len, s->d_queue};
+                        switch (dtype) {
+                        case WN_F32: e = wn::launch_persist_f32(a, bq, c, full, smem, s->sms, cs); break;
+                        case WN_BF16: e = wn::launch_persist_bf16(a, bq, c, full, smem, s->sms, cs); break;
+                        default: e = wn::launch_persist_f16(a, bq, c, full, smem, s->sms, cs); break;
+                        }
+                    }
+                    if (e == cudaSuccess) e = cudaEventRecord(e1, cs);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0) times[rep - 1] = ms;
+                }
+                const float t_ms = std::min(times[0], times[1]);
+                if (e == cudaSuccess && t_ms < best_ms) {
+                    best_ms = t_ms;
+                    best = c;
+                }
+            }
+        chosen[g.N] = best;
+    }
+    if (e == cudaSuccess) e = restore();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (hdr_bak) cudaFree(hdr_bak);
+    if (pool_bak) cudaFree(pool_bak);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail("wn_autotune_batch", e);
+    for (auto &kv : chosen) s->group_cfg[kv.first] = kv.second;
+    if (s->gexec) {  // a captured graph used the old shapes
+        cudaGraphExecDestroy(s->gexec);
+        s->gexec = nullptr;
+    }
     return WN_OK;
 }
 

@@ -31,6 +31,7 @@
 // (Section 5.5); in FP32 the two differ by the rounding of R passes.
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
 
 #include "wn_device.cuh"
@@ -69,7 +70,7 @@ struct CtlState {
     float r;          // reserved value of the block before the call
     float A, B;       // chi-squared (c) constants
     float sc[2];      // output scale of block b, by parity of b
-    float pad_;
+    uint32_t item;    // persistent CTAs: the work item just claimed
 };
 static_assert(sizeof(CtlState) == 48, "CtlState layout");
 
@@ -595,6 +596,80 @@ __global__ void __launch_bounds__(MAXT, MINB) gbm_kernel(GenArgs a, GbmArgs g)
     StreamHdr *h = a.hdr + blockIdx.x;
     run_stream<QT, FULL, float, true>(h, a.pools + h->pool_off, nullptr, 0, a.count, false, a.n_max, a.r_max, g);
 }
+
+// Work of a batch: per stream an output offset (elements from `out`) and a
+// count; `order` lists the streams of one pool size, longest first.
+struct BatchArgs {
+    const uint32_t *order;
+    const uint64_t *offsets;
+    const uint64_t *counts;
+    uint32_t n_items;
+    uint32_t *queue;  // claim counter, zero at launch
+};
+
+// Persistent generate kernel for a batch of uneven requests: each CTA claims
+// the next stream from an atomic counter (longest first), returns that
+// stream's request, and claims again until the list is exhausted.  No CTA
+// waits on another.
+template <int QT, int MAXT, int MINB, bool FULL, typename OutT>
+__global__ void __launch_bounds__(MAXT, MINB) persist_kernel(GenArgs a, BatchArgs bq)
+{
+    CtlState *ctl = reinterpret_cast<CtlState *>(wn_smem + 256);
+    const GbmArgs none{};
+    for (;;) {
+        __syncthreads();  // the previous stream is done with shared memory
+        if (threadIdx.x == 0) ctl->item = atomicAdd(bq.queue, 1u);
+        __syncthreads();
+        const uint32_t it = ctl->item;
+        if (it >= bq.n_items) return;
+        const uint32_t si = bq.order[it];
+        StreamHdr *h = a.hdr + si;
+        const uint64_t off = bq.offsets[si];
+        run_stream<QT, FULL, OutT, false>(h, a.pools + h->pool_off, reinterpret_cast<OutT *>(a.out) + off, off,
+                                          bq.counts[si], true, a.n_max, a.r_max, none);
+    }
+}
+
+template <int QT, int MAXT, int MINB, typename OutT>
+cudaError_t launch_persist_shape(const GenArgs &a, const BatchArgs &bq, uint32_t threads, bool full, size_t smem,
+                                 int sms, cudaStream_t cs)
+{
+    auto kern = full ? persist_kernel<QT, MAXT, MINB, true, OutT> : persist_kernel<QT, MAXT, MINB, false, OutT>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)threads + 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const uint32_t grid = std::min<uint32_t>(bq.n_items, (uint32_t)(per_sm * sms));
+    if (grid == 0) return cudaSuccess;
+    kern<<<grid, threads + 32, smem, cs>>>(a, bq);
+    return cudaGetLastError();
+}
+
+template <typename OutT>
+cudaError_t launch_persist_t(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full, size_t smem,
+                             int sms, cudaStream_t cs)
+{
+    switch (c.qt * 10000 + c.maxt) {
+    case 1 * 10000 + 1024: return launch_persist_shape<1, 1024, 1, OutT>(a, bq, c.threads, full, smem, sms, cs);
+    case 2 * 10000 + 544: return launch_persist_shape<2, 544, 2, OutT>(a, bq, c.threads, full, smem, sms, cs);
+    case 4 * 10000 + 288: return launch_persist_shape<4, 288, 4, OutT>(a, bq, c.threads, full, smem, sms, cs);
+    case 8 * 10000 + 160: return launch_persist_shape<8, 160, 4, OutT>(a, bq, c.threads, full, smem, sms, cs);
+    case 8 * 10000 + 544: return launch_persist_shape<8, 544, 1, OutT>(a, bq, c.threads, full, smem, sms, cs);
+    case 16 * 10000 + 288: return launch_persist_shape<16, 288, 1, OutT>(a, bq, c.threads, full, smem, sms, cs);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_persist_f32(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full, size_t smem,
+                               int sms, cudaStream_t cs);
+cudaError_t launch_persist_bf16(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full, size_t smem,
+                                int sms, cudaStream_t cs);
+cudaError_t launch_persist_f16(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full, size_t smem,
+                               int sms, cudaStream_t cs);
 
 // Shapes of the GBM consumer {quadruples per thread, thread bound, min CTAs
 // per SM}: fewer resident CTAs than generate's, since the per-position sums

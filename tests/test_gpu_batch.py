@@ -1,0 +1,105 @@
+"""Batched uneven requests: persistent kernels per pool size, CUDA graph.
+
+Every stream's slice of the batch output must be the oracle's next values of
+that stream (FP32 within the error model), whatever the mix of pool sizes,
+passes and lengths, including empty requests and partial blocks, and with
+slices packed contiguously so that every alignment occurs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from _parity import assert_fp32_close, passes_fresh
+from paper_1005_2314_gb300.workloads import packed_offsets, uneven_batch
+
+pytestmark = pytest.mark.gpu
+
+
+def _mix(n=36, seed=5):
+    rng = np.random.default_rng(seed)
+    N = rng.choice(np.array([4, 64, 1024, 4096, 16384], dtype=np.uint32), size=n)
+    R = rng.choice(np.array([1, 2, 3, 4], dtype=np.uint32), size=n)
+    counts = rng.integers(0, 40000, size=n).astype(np.uint64)
+    counts[:6] = [0, 1, 3, 1022, 4095, 16383]
+    return N, R, counts
+
+
+def _check(got_flat, N, R, seeds, counts, offsets, first_blocks=None, prefix=None):
+    for i in range(len(N)):
+        c = int(counts[i])
+        if c == 0:
+            continue
+        s = oracle.Stream(int(N[i]), int(R[i]), int(seeds[i]))
+        fb = 0
+        if prefix is not None:
+            s.skip(int(prefix[i]))
+            fb = int(prefix[i]) // (int(N[i]) - 1)
+        ref = s.generate(c)
+        got = got_flat[int(offsets[i]): int(offsets[i]) + c]
+        # values of a block begun before this call were formed in earlier blocks
+        assert_fp32_close(got, ref, passes_fresh(c, int(N[i]), int(R[i]), first_block=fb) + int(R[i]),
+                          f"stream {i} N={N[i]} R={R[i]}")
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_matches_oracle_and_continues(wn, use_graph):
+    import torch
+    N, R, counts = _mix()
+    seeds = np.arange(100, 100 + len(N))
+    offsets = packed_offsets(counts)
+    total = int(counts.sum())
+    h = wn.wn_create_streams(N, R, seeds)
+    out = torch.zeros(total + 8, dtype=torch.float32, device="cuda")
+    wn.wn_generate_batch(out, counts, offsets, h, use_graph=use_graph)
+    torch.cuda.synchronize()
+    _check(out.cpu().numpy(), N, R, seeds, counts, offsets)
+    # a second call (a graph replay when use_graph) continues every stream
+    wn.wn_generate_batch(out, counts, offsets, h, use_graph=use_graph)
+    torch.cuda.synchronize()
+    _check(out.cpu().numpy(), N, R, seeds, counts, offsets, prefix=counts)
+
+
+def test_graph_recaptures_on_new_arguments(wn):
+    import torch
+    N, R, counts = _mix(12, seed=9)
+    seeds = np.arange(7, 7 + len(N))
+    h = wn.wn_create_streams(N, R, seeds)
+    off1 = packed_offsets(counts)
+    out = torch.zeros(int(counts.sum()) * 2 + 8, dtype=torch.float32, device="cuda")
+    wn.wn_generate_batch(out, counts, off1, h, use_graph=True)
+    counts2 = counts[::-1].copy()
+    off2 = packed_offsets(counts2) + 3  # other lengths, shifted alignment
+    wn.wn_generate_batch(out, counts2, off2, h, use_graph=True)
+    torch.cuda.synchronize()
+    _check(out.cpu().numpy(), N, R, seeds, counts2, off2, prefix=counts)
+
+
+def test_autotune_batch_keeps_state(wn):
+    import torch
+    N, R, counts = _mix(20, seed=11)
+    seeds = np.arange(50, 50 + len(N))
+    h = wn.wn_create_streams(N, R, seeds)
+    offsets = packed_offsets(counts)
+    out = torch.zeros(int(counts.sum()) + 8, dtype=torch.float32, device="cuda")
+    before = [wn.wn_get_state(h, i) for i in range(len(N))]
+    wn.wn_autotune_batch(out, counts, offsets, h)
+    assert [wn.wn_get_state(h, i) for i in range(len(N))] == before
+    wn.wn_generate_batch(out, counts, offsets, h, use_graph=True)
+    torch.cuda.synchronize()
+    _check(out.cpu().numpy(), N, R, seeds, counts, offsets)
+
+
+def test_uneven_recipe_scaled_down(wn):
+    # the batched-request recipe (pool from {1024, 4096, 16384}, R from
+    # {1, 2, 4}, log-uniform lengths) at 300 streams and lengths 2^10..2^16
+    import torch
+    N, R, counts = uneven_batch(300, seed=12345, log2_max=16.0)
+    seeds = np.arange(1, 301)
+    offsets = packed_offsets(counts)
+    h = wn.wn_create_streams(N, R, seeds)
+    out = torch.zeros(int(counts.sum()) + 8, dtype=torch.float32, device="cuda")
+    wn.wn_generate_batch(out, counts, offsets, h, use_graph=True)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    pick = np.arange(0, 300, 37)
+    _check(got, N[pick], R[pick], seeds[pick], counts[pick], offsets[pick])
