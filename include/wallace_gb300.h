@@ -128,6 +128,30 @@ wn_status wn_generate_batch(void *out, const uint64_t *counts, const uint64_t *o
                             wn_dtype dtype, int use_graph, void *cuda_stream);
 
 /*
+ * wn_generate_batch_noalloc -- the same work as wn_generate_batch with
+ * use_graph = 0, for callers that must not allocate device memory: code whose
+ * device memory is already fully claimed by another allocator (a framework's
+ * caching pool, a fixed budget per tenant), and latency-critical serving
+ * loops that cannot afford cudaMalloc, which blocks the calling thread and
+ * can synchronise the device.  This call makes no cudaMalloc or cudaFree and
+ * no other allocating call (nor does it create streams or events): the claim
+ * counters and the request descriptors live in one fixed array of device
+ * memory compiled into the library (about 320 KB, resident on every device
+ * that loads the library until the process exits), so it serves at most
+ * WN_NOALLOC_MAX_STREAMS streams (WN_EINVAL beyond, or with more pool sizes
+ * than the array's 16 counters).  The groups run one after another on
+ * cuda_stream.  The first call on a device looks up the array's device
+ * address there (with that device current); make that first call before any
+ * stream capture.  Every call shares the array: calls whose work overlaps on
+ * the GPU (e.g. on two CUDA streams at once) race on it, so order them on one
+ * stream or synchronise in between.  The handle's device must be current.
+ * The paper has no counterpart to this entry point.
+ */
+#define WN_NOALLOC_MAX_STREAMS 16384u
+wn_status wn_generate_batch_noalloc(void *out, const uint64_t *counts, const uint64_t *offsets, wn_stream *s,
+                                    wn_dtype dtype, void *cuda_stream);
+
+/*
  * wn_autotune_batch -- picks, for each pool size of the batch described by
  * out/counts/offsets/dtype (as in wn_generate_batch), the compiled launch
  * shape whose persistent kernel serves that group fastest, timing each on a

@@ -25,7 +25,7 @@ __all__ = [
     "wn_create", "wn_create_streams", "wn_destroy", "wn_generate", "wn_generate_ex",
     "wn_generate_host",
     "wn_set_cuda_stream", "wn_set_config", "wn_get_config", "wn_autotune", "wn_gbm", "wn_generate_batch",
-    "wn_autotune_batch", "wn_num_streams", "wn_get_pool", "wn_get_state",
+    "wn_autotune_batch", "wn_generate_batch_noalloc", "wn_num_streams", "wn_get_pool", "wn_get_state",
     "wn_rng_draws", "wn_boxmuller", "wn_last_error", "library_path", "load",
 ]
 
@@ -63,6 +63,7 @@ def _load() -> ctypes.CDLL:
         "wn_autotune": (_i, [_p, _u64, _i, _p, _p, _p]),
         "wn_generate_batch": (_i, [_p, _p, _p, _p, _i, _i, _p]),
         "wn_autotune_batch": (_i, [_p, _p, _p, _p, _i, _p]),
+        "wn_generate_batch_noalloc": (_i, [_p, _p, _p, _p, _i, _p]),
         "wn_gbm": (_i, [_p, _p, _u32, _u32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                         ctypes.c_double, _p]),
         "wn_num_streams": (_u32, [_p]),
@@ -244,6 +245,18 @@ def wn_generate_batch(out, counts, offsets, h: Handle, dtype: int = WN_F32, use_
     counts, offsets, need = _batch_arrays(h, counts, offsets)
     _check(_L().wn_generate_batch(_out_ptr(out, need, dtype), counts.ctypes.data, offsets.ctypes.data, h.ptr,
                                   dtype, int(bool(use_graph)), _stream_ptr(cuda_stream)), "wn_generate_batch")
+
+
+def wn_generate_batch_noalloc(out, counts, offsets, h: Handle, dtype: int = WN_F32, cuda_stream=None) -> None:
+    """As wn_generate_batch without a graph, for callers that must not
+    allocate device memory: the library's fixed scratch array holds the
+    request descriptors (at most WN_NOALLOC_MAX_STREAMS = 16384 streams)."""
+    counts, offsets, need = _batch_arrays(h, counts, offsets)
+    _check(_L().wn_generate_batch_noalloc(_out_ptr(out, need, dtype), counts.ctypes.data, offsets.ctypes.data,
+                                          h.ptr, dtype, _stream_ptr(cuda_stream)), "wn_generate_batch_noalloc")
+
+
+WN_NOALLOC_MAX_STREAMS = 16384
 
 
 def wn_autotune_batch(out, counts, offsets, h: Handle, dtype: int = WN_F32, cuda_stream=None) -> None:

@@ -346,6 +346,49 @@ wn_status check_batch_args(const wn_stream *s, const void *out, const uint64_t *
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Scratch for wn_generate_batch_noalloc: a fixed device array instead of
+// memory the library allocates.  Layout: 16 claim counters (one per pool-size
+// group) in the first 256 bytes, then the claim order (uint32), the output
+// offsets and the counts (uint64) of up to WN_NOALLOC_MAX_STREAMS streams.
+// Every call shares it.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kNaCounters = 0;
+constexpr size_t kNaOrder = 256;
+constexpr size_t kNaOffsets = kNaOrder + 4 * (size_t)WN_NOALLOC_MAX_STREAMS;
+constexpr size_t kNaCounts = kNaOffsets + 8 * (size_t)WN_NOALLOC_MAX_STREAMS;
+constexpr size_t kNaBytes = kNaCounts + 8 * (size_t)WN_NOALLOC_MAX_STREAMS;
+}  // namespace
+
+static __device__ __align__(256) unsigned char wn_noalloc_scratch[kNaBytes];
+
+namespace {
+// Device address of wn_noalloc_scratch on each device, looked up once per
+// device (with that device current) on the first call there.  In host code
+// the array's name is only a host-side stand-in, never a device address.
+std::mutex g_na_mu;
+unsigned char *g_na_ptr[128] = {};
+// host-side claim order of the call in progress (static storage: nothing is
+// allocated per call); calls are serialised on g_na_plan_mu
+std::mutex g_na_plan_mu;
+uint32_t g_na_order[WN_NOALLOC_MAX_STREAMS];
+
+wn_status noalloc_scratch(int dev, unsigned char **ptr)
+{
+    if (dev < 0 || dev >= 128) return fail(WN_EINVAL, "wn_generate_batch_noalloc: device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_na_mu);
+    if (!g_na_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, wn_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail("wn_generate_batch_noalloc: cudaGetSymbolAddress", e);
+        g_na_ptr[dev] = static_cast<unsigned char *>(p);
+    }
+    *ptr = g_na_ptr[dev];
+    return WN_OK;
+}
+}  // namespace
+
 extern "C" {
 
 const char *wn_last_error(void) { return g_err.c_str(); }
@@ -814,6 +857,76 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
         cudaGraphExecDestroy(s->gexec);
         s->gexec = nullptr;
     }
+    return WN_OK;
+}
+
+wn_status wn_generate_batch_noalloc(void *out, const uint64_t *counts, const uint64_t *offsets, wn_stream *s,
+                                    wn_dtype dtype, void *cuda_stream)
+{
+    wn_status st = check_batch_args(s, out, counts, offsets, dtype);
+    if (st != WN_OK) return st;
+    if (s->n > WN_NOALLOC_MAX_STREAMS)
+        return fail(WN_EINVAL, "wn_generate_batch_noalloc: " + std::to_string(s->n) + " streams exceed the " +
+                                   std::to_string(WN_NOALLOC_MAX_STREAMS) + " its fixed scratch array holds");
+    int dev = -1;
+    WN_CU(cudaGetDevice(&dev));
+    if (dev != s->device)
+        return fail(WN_EINVAL, "wn_generate_batch_noalloc: the handle's device must be current");
+    unsigned char *scratch = nullptr;
+    if ((st = noalloc_scratch(dev, &scratch)) != WN_OK) return st;
+    // Plan without heap allocation: pool sizes are powers of two 4..16384
+    // (13 groups, indexed by log2 N - 2); each group's streams in claim order,
+    // longest request first (ties by stream index; std::sort sorts in place).
+    std::lock_guard<std::mutex> plan_lock(g_na_plan_mu);
+    uint32_t *order = g_na_order;
+    uint32_t cnt[13] = {}, start[13] = {}, fill[13] = {}, rmax[13] = {};
+    auto gidx = [](uint32_t N) {
+        uint32_t g = 0;
+        while ((4u << g) < N) ++g;
+        return g;
+    };
+    for (uint32_t i = 0; i < s->n; ++i) {
+        const uint32_t g = gidx(s->N[i]);
+        ++cnt[g];
+        rmax[g] = std::max(rmax[g], s->R[i]);
+    }
+    for (uint32_t g = 1; g < 13; ++g) start[g] = start[g - 1] + cnt[g - 1];
+    for (uint32_t i = 0; i < s->n; ++i) {
+        const uint32_t g = gidx(s->N[i]);
+        order[start[g] + fill[g]++] = i;
+    }
+    for (uint32_t g = 0; g < 13; ++g)
+        std::sort(order + start[g], order + start[g] + cnt[g], [&](uint32_t x, uint32_t y) {
+            const uint64_t cx = counts[x] * (s->R[x] + 1ull), cy = counts[y] * (s->R[y] + 1ull);
+            return cx != cy ? cx > cy : x < y;
+        });
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(cuda_stream);
+    uint32_t *d_counters = reinterpret_cast<uint32_t *>(scratch + kNaCounters);
+    uint32_t *d_order = reinterpret_cast<uint32_t *>(scratch + kNaOrder);
+    uint64_t *d_offsets = reinterpret_cast<uint64_t *>(scratch + kNaOffsets);
+    uint64_t *d_counts = reinterpret_cast<uint64_t *>(scratch + kNaCounts);
+    WN_CU(cudaMemcpyAsync(d_counts, counts, sizeof(uint64_t) * s->n, cudaMemcpyHostToDevice, cs));
+    WN_CU(cudaMemcpyAsync(d_offsets, offsets, sizeof(uint64_t) * s->n, cudaMemcpyHostToDevice, cs));
+    WN_CU(cudaMemcpyAsync(d_order, order, sizeof(uint32_t) * s->n, cudaMemcpyHostToDevice, cs));
+    // the claim counters must start at zero; the array keeps the last call's values
+    WN_CU(cudaMemsetAsync(d_counters, 0, 256, cs));
+    for (uint32_t g = 0; g < 13; ++g) {
+        if (cnt[g] == 0) continue;
+        const uint32_t N = 4u << g;
+        wn::GenArgs a{s->d_hdr, s->d_pools, out, 0, 0, cnt[g], N, rmax[g], 0};
+        wn::BatchArgs bq{d_order + start[g], d_offsets, d_counts, cnt[g], d_counters + g};
+        const LaunchCfg c = group_cfg(s, N);
+        const bool full = (uint64_t)c.threads * c.qt == N / 4;
+        const size_t smem = wn::gen_smem_bytes(s->smem_base, N, rmax[g]);
+        cudaError_t e;
+        switch (dtype) {
+        case WN_F32: e = wn::launch_persist_f32(a, bq, c, full, smem, s->sms, cs); break;
+        case WN_BF16: e = wn::launch_persist_bf16(a, bq, c, full, smem, s->sms, cs); break;
+        default: e = wn::launch_persist_f16(a, bq, c, full, smem, s->sms, cs); break;
+        }
+        if (e != cudaSuccess) return cuda_fail("wn_generate_batch_noalloc: launch", e);
+    }
+    for (uint32_t i = 0; i < s->n; ++i) advance_k_one(s, i, counts[i]);
     return WN_OK;
 }
 
