@@ -197,6 +197,25 @@ def oracle_sample(n_streams: int, per_stream: int, steps: int, warmup: int, thre
 
 
 # ---------------------------------------------------------------------------
+# Rank logic (weak scaling: ranks shard independent streams)
+# ---------------------------------------------------------------------------
+
+def rank_seeds(rank: int, streams: int):
+    """Seeds of rank `rank`'s streams: disjoint ranges, 1-based."""
+    return [rank * streams + i + 1 for i in range(streams)]
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Maximum of a per-rank float over all ranks (the timing reduction)."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------
 
@@ -208,7 +227,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
     STREAMS, PER_STREAM = args.streams, args.per_stream
-    seeds = [rank * STREAMS + i + 1 for i in range(STREAMS)]
+    seeds = rank_seeds(rank, STREAMS)
 
     t0 = time.perf_counter()
     h = wn.wn_create_streams([POOL_N] * STREAMS, [PASSES_R] * STREAMS, seeds, WARMUP_BLOCKS, stream)
@@ -243,11 +262,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     variates = STREAMS * PER_STREAM
     value = world * variates * args.steps / (total_ms / 1e3)
     ms_per_step = total_ms / args.steps
@@ -309,11 +324,7 @@ def run_ours(args, rank, world, local_rank):
         for _ in range(e_steps):
             wn.wn_generate_host(host, PER_STREAM, h, wn.WN_F32, stream)
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t
-        if world > 1:
-            tt = torch.tensor([dt], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            dt = float(tt.item())
+        dt = max_over_ranks(time.perf_counter() - t, world, dev)
         e2e = {"value": world * variates * e_steps / dt, "unit": "variates/s", "h2d_bytes_per_step": 0,
                "d2h_bytes_per_step": variates * 4, "steps": e_steps,
                "how": "wn_generate_host into pinned host memory: generation in 256 MiB chunks with "
