@@ -237,8 +237,8 @@ struct GbmArgs {
 // the buffer at window address rd, store the four results contiguously into
 // the buffer at wr.  All gathers are issued before any arithmetic.  The
 // update y_k = s_k (S/2 - a_k), S = a_0 + a_1 + a_2 + a_3, is computed as
-// m_k a_k + m_k (-S/2), m_k = -s_k (both products exact, so the one rounding
-// is that of S/2 - a_k).
+// m_k a_k + h_k S with m_k = -s_k and h_k = -m_k/2 (both products exact, so
+// the one rounding is that of S/2 - a_k).
 //
 // The final pass of a block (FINAL) also sums the squares of its results
 // (the next block's renormalisation) and, when EMIT is set, writes the
@@ -264,6 +264,7 @@ __device__ __forceinline__ void pass_quads(uint32_t rd, uint32_t wr, uint32_t ta
     const uint4 P = lds4u(tab);
     const float4 sg = lds4(tab + 16u + 16u * (lane & 15u));
     const float2 m01 = make_float2(sg.x, sg.y), m23 = make_float2(sg.z, sg.w);
+    const float2 h01 = fmul2(m01, make_float2(-0.5f, -0.5f)), h23 = fmul2(m23, make_float2(-0.5f, -0.5f));
     const uint32_t B0 = P.x * q0 + P.y;
     float a[QT][4];
 #pragma unroll
@@ -286,10 +287,10 @@ __device__ __forceinline__ void pass_quads(uint32_t rd, uint32_t wr, uint32_t ta
         const uint32_t q = q0 + 32u * j;
         const float2 a01 = make_float2(a[j][0], a[j][1]), a23 = make_float2(a[j][2], a[j][3]);
         const float2 s2 = fadd2(a01, a23);
-        const float nh = -0.5f * (s2.x + s2.y);
-        const float2 NH = make_float2(nh, nh);
-        y[j][0] = ffma2(m01, a01, fmul2(m01, NH));
-        y[j][1] = ffma2(m23, a23, fmul2(m23, NH));
+        const float sum = s2.x + s2.y;
+        const float2 SS = make_float2(sum, sum);
+        y[j][0] = ffma2(m01, a01, fmul2(h01, SS));
+        y[j][1] = ffma2(m23, a23, fmul2(h23, SS));
         if (FULL || q < nq) {
             sts4(wr + 16u * q, y[j][0], y[j][1]);
             if (FINAL) part = ffma2(y[j][0], y[j][0], ffma2(y[j][1], y[j][1], part));
