@@ -219,6 +219,78 @@ def max_over_ranks(x: float, world: int, device=None) -> float:
 # Our arm
 # ---------------------------------------------------------------------------
 
+def _timed(torch, stream, flush, fn, reps):
+    """Median CUDA-event time (ms) of fn() on `stream`, L2 flushed before each."""
+    ms = []
+    for i in range(reps):
+        flush.fill_(i & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        ms.append((a, b))
+    torch.cuda.synchronize()
+    t = sorted(x.elapsed_time(y) for x, y in ms)
+    return t[len(t) // 2]
+
+
+def other_workloads(wn, torch, dev, stream, flush):
+    """The method's other workloads on this GPU, each timed with CUDA events:
+    one stream (pool 1024, R=2, 2^24 FP32 in one call); 4096 streams of pool
+    16384, R=3, 2^21 values each in BF16 and in FP16 (with Box-Muller at the
+    same shape and type); and the fused GBM consumer (2^20 paths x 252 steps,
+    pool 4096, R=2, normals never written to memory)."""
+    peak, _ = _peaks()
+    res = {}
+    # single stream: a serial chain of blocks on one SM
+    h1 = wn.wn_create(1024, 2, 1)
+    wn.wn_set_cuda_stream(h1, stream)
+    n1 = 1 << 24
+    o1 = torch.empty(n1, dtype=torch.float32, device=dev)
+    shape1 = wn.wn_autotune(h1, n1, wn.WN_F32, stream)
+    wn.wn_generate_ex(o1, n1, h1, wn.WN_F32, stream)
+    t1 = _timed(torch, stream, flush, lambda: wn.wn_generate_ex(o1, n1, h1, wn.WN_F32, stream), 5)
+    res["single_stream"] = {"value": n1 / (t1 / 1e3), "unit": "variates/s", "ms_per_call": t1,
+                            "config": "1 stream, pool N=1024, R=2, seed 1, 2^24 FP32 per call",
+                            "shape": list(shape1)}
+    wn.wn_destroy(h1)
+    del o1
+    # 16-bit outputs from an FP32 pool
+    S3, N3, R3, per3 = 4096, 16384, 3, 1 << 21
+    h3 = wn.wn_create_streams([N3] * S3, [R3] * S3, list(range(1, S3 + 1)), WARMUP_BLOCKS, stream)
+    o3 = torch.empty(S3 * per3, dtype=torch.bfloat16, device=dev)
+    prec = {}
+    for dt, name, tdt in ((wn.WN_BF16, "bf16", torch.bfloat16), (wn.WN_F16, "f16", torch.float16)):
+        o = o3.view(tdt)
+        shape3 = wn.wn_autotune(h3, 1 << 16, dt, stream)
+        wn.wn_generate_ex(o, per3, h3, dt, stream)
+        t3 = _timed(torch, stream, flush, lambda: wn.wn_generate_ex(o, per3, h3, dt, stream), 5)
+        tb = _timed(torch, stream, flush, lambda: wn.wn_boxmuller(o, per3, S3, 1, dt, stream), 5)
+        v = S3 * per3 / (t3 / 1e3)
+        prec[name] = {"value": v, "unit": "variates/s", "ms_per_step": t3, "shape": list(shape3),
+                      "hbm_frac": round(v * 2 / 1e9 / peak, 4),
+                      "boxmuller_value": S3 * per3 / (tb / 1e3), "wallace_over_boxmuller": tb / t3}
+    prec["config"] = "4096 streams x pool N=16384, R=3, 2^21 values each (2^33 per type), FP32 pool, 16-bit RN output"
+    res["precision"] = prec
+    wn.wn_destroy(h3)
+    del o3
+    # fused consumer: geometric Brownian motion driven in-kernel
+    N5, R5, ppg, steps, paths = 4096, 2, 455, 252, 1 << 20
+    G = -(-paths // ppg)
+    h5 = wn.wn_create_streams([N5] * G, [R5] * G, list(range(1, G + 1)), WARMUP_BLOCKS, stream)
+    st = torch.empty(G * ppg, dtype=torch.float32, device=dev)
+    args5 = (0.05, 0.2, 1.0 / 252)
+    wn.wn_gbm(st, h5, ppg, steps, 100.0, *args5, stream)
+    t5 = _timed(torch, stream, flush, lambda: wn.wn_gbm(st, h5, ppg, steps, 100.0, *args5, stream), 5)
+    res["gbm"] = {"value": G * ppg * steps / (t5 / 1e3), "unit": "normals consumed/s", "ms_per_call": t5,
+                  "paths_per_s": G * ppg / (t5 / 1e3),
+                  "config": f"{G * ppg} paths ({G} streams x {ppg}) x 252 steps, pool N=4096, R=2, "
+                            "S0=100, mu=0.05, sigma=0.2, dt=1/252"}
+    wn.wn_destroy(h5)
+    return res
+
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1005_2314_gb300 as wn
@@ -334,6 +406,12 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": None, "unit": "variates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
                "error": str(ex)[:200]}
 
+    # the other workloads of the method, one line each (the headline stays the
+    # many-streams FP32 step above)
+    configs = None
+    if not args.no_configs:
+        configs = other_workloads(wn, torch, dev, stream, flush)
+
     # the batched uneven-request workload: 10,000 streams, pool from
     # {1024, 4096, 16384}, R from {1, 2, 4}, log-uniform lengths 2^10..2^24,
     # FP32 packed contiguously; one captured graph of persistent kernels
@@ -387,6 +465,7 @@ def run_ours(args, rank, world, local_rank):
                                                        "ms_per_step": bm_step,
                                                        "wallace_over_boxmuller": value / world / bm_value}},
             "batched_uneven": batched,
+            "workloads": configs,
             "create_s": create_s,
             "context": {"torch_fill_write_gbs": round(fill_gbs, 1),
                         "frac_of_fill": round(achieved / fill_gbs, 4)}}
@@ -423,6 +502,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-request leg")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the single-stream, 16-bit and fused-GBM workload legs")
     ap.add_argument("--streams", type=int, default=STREAMS, help="streams per GPU (default 4096)")
     ap.add_argument("--per-stream", type=int, default=PER_STREAM, help="values per stream per step")
     ap.add_argument("--shape", default="",
