@@ -230,6 +230,31 @@ wn_status wn_get_state(const wn_stream *s, uint32_t i, uint64_t *host_xw, double
                        float *host_scale, uint32_t *host_k, uint64_t *host_blocks);
 
 /*
+ * wn_save -- checkpoint: serialise the complete state of every stream of the
+ * handle (generator words, Section 5.8; pool, reserved value, sum of squares,
+ * block count and the position within the last block, Section 5.5) into the
+ * caller's host buffer.  Synchronises the handle's CUDA stream first, so the
+ * state includes every call enqueued before.  With host_buf == NULL only
+ * *bytes_needed is set.  Layout (little-endian, version 1): 8-byte magic
+ * "WNSTATE1", uint32 stream count, uint32 header size (96), the 96-byte
+ * per-stream headers, the pools as FP32 in stream order, and an FNV-1a 64
+ * checksum of everything before it.  WN_EINVAL if buf_bytes is too small.
+ */
+wn_status wn_save(const wn_stream *s, void *host_buf, uint64_t buf_bytes, uint64_t *bytes_needed);
+
+/*
+ * wn_load -- resume: a new handle whose streams continue exactly where the
+ * saved ones stood (the next call returns, bit for bit, what the saved
+ * handle's next call would have).  The buffer is validated before any
+ * device memory is touched: magic, version, sizes, checksum, pool sizes
+ * (powers of two in [4, 16384]), pass counts, positions and generator words;
+ * a corrupt buffer returns NULL with the reason in wn_last_error().  The
+ * handle is created on the current device; the copies run on cuda_stream,
+ * which is then synchronised.
+ */
+wn_stream *wn_load(const void *host_buf, uint64_t buf_bytes, void *cuda_stream);
+
+/*
  * wn_rng_draws -- the first n 64-bit draws of the stream generator seeded by
  * `seed` (SplitMix64 seeding, xorshift64 (13,7,17) + Weyl), computed on the
  * device and copied to host_out.  For checking the integer stream

@@ -26,7 +26,7 @@ __all__ = [
     "wn_generate_host",
     "wn_set_cuda_stream", "wn_set_config", "wn_get_config", "wn_autotune", "wn_gbm", "wn_generate_batch",
     "wn_autotune_batch", "wn_generate_batch_noalloc", "wn_num_streams", "wn_get_pool", "wn_get_state",
-    "wn_rng_draws", "wn_boxmuller", "wn_last_error", "library_path", "load",
+    "wn_rng_draws", "wn_boxmuller", "wn_save", "wn_load", "wn_last_error", "library_path", "load",
 ]
 
 WN_F32, WN_BF16, WN_F16 = 0, 1, 2
@@ -71,6 +71,8 @@ def _load() -> ctypes.CDLL:
         "wn_get_state": (_i, [_p, _u32, _p, _p, _p, _p, _p]),
         "wn_rng_draws": (_i, [_u64, _u64, _p]),
         "wn_boxmuller": (_i, [_p, _u64, _u32, _u64, _i, _p]),
+        "wn_save": (_i, [_p, _p, _u64, _p]),
+        "wn_load": (_p, [_p, _u64, _p]),
         "wn_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -299,6 +301,26 @@ def wn_rng_draws(seed: int, n: int) -> np.ndarray:
     out = np.zeros(n, dtype=np.uint64)
     _check(_L().wn_rng_draws(seed, n, out.ctypes.data), "wn_rng_draws")
     return out
+
+
+def wn_save(h: Handle) -> np.ndarray:
+    """The handle's complete state as a uint8 array (synchronises its CUDA stream)."""
+    need = ctypes.c_uint64(0)
+    _check(_L().wn_save(h.ptr, None, 0, ctypes.byref(need)), "wn_save")
+    buf = np.empty(need.value, dtype=np.uint8)
+    _check(_L().wn_save(h.ptr, buf.ctypes.data, buf.size, None), "wn_save")
+    return buf
+
+
+def wn_load(buf, cuda_stream=None) -> Handle:
+    """A new handle continuing the streams saved in `buf` (bytes or a uint8 array)."""
+    arr = np.ascontiguousarray(np.frombuffer(bytes(buf), dtype=np.uint8) if isinstance(buf, (bytes, bytearray))
+                               else np.asarray(buf, dtype=np.uint8))
+    p = _L().wn_load(arr.ctypes.data if arr.size else None, arr.size, _stream_ptr(cuda_stream))
+    if not p:
+        raise WnError(f"wn_load: {wn_last_error()}")
+    n = _L().wn_num_streams(p)
+    return Handle(p, n)
 
 
 def wn_boxmuller(out, count: int, n_streams: int, seed: int, dtype: int = WN_F32, cuda_stream=None) -> None:

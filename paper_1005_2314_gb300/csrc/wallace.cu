@@ -389,50 +389,41 @@ wn_status noalloc_scratch(int dev, unsigned char **ptr)
 }
 }  // namespace
 
-extern "C" {
+extern "C" void wn_destroy(wn_stream *s);
 
-const char *wn_last_error(void) { return g_err.c_str(); }
-
-wn_stream *wn_create_streams(uint32_t n_streams, const uint32_t *pool_N, const uint32_t *passes_R,
-                             const uint64_t *seeds, uint32_t warmup_blocks, void *cuda_stream)
+// A handle for n streams of the given pool sizes and pass counts: validates
+// them, allocates headers and pools (contents unset), probes where dynamic
+// shared memory starts and checks that the generate kernel's layout fits.
+// NULL (with the error recorded under `who`) on failure.
+wn_stream *alloc_handle(uint32_t n_streams, const uint32_t *pool_N, const uint32_t *passes_R, cudaStream_t cs,
+                        const char *who)
 {
-    g_err.clear();
-    if (n_streams == 0 || !pool_N || !passes_R || !seeds) {
-        fail(WN_EINVAL, "wn_create_streams: empty stream set or NULL array");
-        return nullptr;
-    }
+    const std::string w(who);
+    for (uint32_t i = 0; i < n_streams; ++i)
+        if (!valid_pool(pool_N[i]) || !valid_passes(passes_R[i])) {
+            fail(WN_EINVAL, w + ": stream " + std::to_string(i) +
+                                ": pool_N must be a power of two in [4, 16384] and passes_R in [1, 64]");
+            return nullptr;
+        }
     wn_stream *s = new wn_stream();
     s->n = n_streams;
     s->N.assign(pool_N, pool_N + n_streams);
-    s->k_host.resize(n_streams);
-    for (uint32_t i = 0; i < n_streams; ++i) s->k_host[i] = pool_N[i] - 1;
     s->R.assign(passes_R, passes_R + n_streams);
-    std::vector<wn::StreamHdr> h(n_streams);
+    s->k_host.resize(n_streams);
     uint64_t off = 0;
     for (uint32_t i = 0; i < n_streams; ++i) {
-        if (!valid_pool(pool_N[i]) || !valid_passes(passes_R[i])) {
-            fail(WN_EINVAL, "wn_create_streams: stream " + std::to_string(i) +
-                                ": pool_N must be a power of two in [4, 16384] and passes_R in [1, 64]");
-            delete s;
-            return nullptr;
-        }
-        std::memset(&h[i], 0, sizeof(h[i]));
-        h[i].x = seeds[i];  // consumed by the init kernel
-        h[i].N = pool_N[i];
-        h[i].R = passes_R[i];
-        h[i].pool_off = off;
+        s->k_host[i] = pool_N[i] - 1;
         off += pool_N[i];
         s->n_max = std::max(s->n_max, pool_N[i]);
         if (pool_N[i] != pool_N[0]) s->uniform_N = false;
         s->r_max = std::max(s->r_max, passes_R[i]);
     }
-    cudaStream_t cs = reinterpret_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_hdr, sizeof(wn::StreamHdr) * n_streams);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_pools, sizeof(float) * off);
     if (e != cudaSuccess) {
-        cuda_fail("wn_create_streams: allocation", e);
+        cuda_fail((w + ": allocation").c_str(), e);
         wn_destroy(s);
         return nullptr;
     }
@@ -449,16 +440,45 @@ wn_stream *wn_create_streams(uint32_t n_streams, const uint32_t *pool_N, const u
         if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
         if (d_base) cudaFree(d_base);
         if (e != cudaSuccess) {
-            cuda_fail("wn_create_streams: shared-memory probe", e);
+            cuda_fail((w + ": shared-memory probe").c_str(), e);
             wn_destroy(s);
             return nullptr;
         }
     }
     if (wn::gen_smem_bytes(s->smem_base, s->n_max, s->r_max) > 227u * 1024u) {
-        fail(WN_EINVAL, "wn_create_streams: pool and pass counts need more shared memory than a CTA has");
+        fail(WN_EINVAL, w + ": pool and pass counts need more shared memory than a CTA has");
         wn_destroy(s);
         return nullptr;
     }
+    return s;
+}
+
+extern "C" {
+
+const char *wn_last_error(void) { return g_err.c_str(); }
+
+wn_stream *wn_create_streams(uint32_t n_streams, const uint32_t *pool_N, const uint32_t *passes_R,
+                             const uint64_t *seeds, uint32_t warmup_blocks, void *cuda_stream)
+{
+    g_err.clear();
+    if (n_streams == 0 || !pool_N || !passes_R || !seeds) {
+        fail(WN_EINVAL, "wn_create_streams: empty stream set or NULL array");
+        return nullptr;
+    }
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(cuda_stream);
+    wn_stream *s = alloc_handle(n_streams, pool_N, passes_R, cs, "wn_create_streams");
+    if (!s) return nullptr;
+    std::vector<wn::StreamHdr> h(n_streams);
+    uint64_t off = 0;
+    for (uint32_t i = 0; i < n_streams; ++i) {
+        std::memset(&h[i], 0, sizeof(h[i]));
+        h[i].x = seeds[i];  // consumed by the init kernel
+        h[i].N = pool_N[i];
+        h[i].R = passes_R[i];
+        h[i].pool_off = off;
+        off += pool_N[i];
+    }
+    cudaError_t e;
     e = cudaMemcpyAsync(s->d_hdr, h.data(), sizeof(wn::StreamHdr) * n_streams, cudaMemcpyHostToDevice, cs);
     const size_t ismem = sizeof(int32_t) * s->n_max;
     if (e == cudaSuccess && ismem > 48 * 1024)
@@ -479,6 +499,121 @@ wn_stream *wn_create_streams(uint32_t n_streams, const uint32_t *pool_N, const u
     e = cudaStreamSynchronize(cs);
     if (e != cudaSuccess) {
         cuda_fail("wn_create_streams: synchronize", e);
+        wn_destroy(s);
+        return nullptr;
+    }
+    return s;
+}
+
+namespace {
+constexpr char kSaveMagic[8] = {'W', 'N', 'S', 'T', 'A', 'T', 'E', '1'};
+
+uint64_t fnv1a64(const unsigned char *p, size_t n)
+{
+    uint64_t h = 0xcbf29ce484222325ull;
+    for (size_t i = 0; i < n; ++i) h = (h ^ p[i]) * 0x100000001b3ull;
+    return h;
+}
+}  // namespace
+
+wn_status wn_save(const wn_stream *s, void *host_buf, uint64_t buf_bytes, uint64_t *bytes_needed)
+{
+    if (!s) return fail(WN_EINVAL, "wn_save: NULL handle");
+    uint64_t pool_elems = 0;
+    for (uint32_t i = 0; i < s->n; ++i) pool_elems += s->N[i];
+    const uint64_t need = 16 + (uint64_t)sizeof(wn::StreamHdr) * s->n + 4 * pool_elems + 8;
+    if (bytes_needed) *bytes_needed = need;
+    if (!host_buf) return WN_OK;
+    if (buf_bytes < need) return fail(WN_EINVAL, "wn_save: buffer holds " + std::to_string(buf_bytes) +
+                                                     " bytes, the state needs " + std::to_string(need));
+    unsigned char *b = static_cast<unsigned char *>(host_buf);
+    std::memcpy(b, kSaveMagic, 8);
+    const uint32_t n = s->n, hb = (uint32_t)sizeof(wn::StreamHdr);
+    std::memcpy(b + 8, &n, 4);
+    std::memcpy(b + 12, &hb, 4);
+    cudaError_t e = cudaStreamSynchronize(s->cs);
+    if (e == cudaSuccess) e = cudaMemcpy(b + 16, s->d_hdr, (size_t)hb * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b + 16 + (size_t)hb * n, s->d_pools, 4 * pool_elems, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail("wn_save: copy", e);
+    wn::StreamHdr *h = reinterpret_cast<wn::StreamHdr *>(b + 16);
+    for (uint32_t i = 0; i < n; ++i) {
+        if (h[i].flags != 0) return fail(WN_EINVAL, "wn_save: stream " + std::to_string(i) + " carries an error flag");
+        h[i].pool_off = 0;  // assigned again on load
+    }
+    const uint64_t sum = fnv1a64(b, need - 8);
+    std::memcpy(b + need - 8, &sum, 8);
+    return WN_OK;
+}
+
+wn_stream *wn_load(const void *host_buf, uint64_t buf_bytes, void *cuda_stream)
+{
+    g_err.clear();
+    const unsigned char *b = static_cast<const unsigned char *>(host_buf);
+    if (!b || buf_bytes < 16 + 8) {
+        fail(WN_EINVAL, "wn_load: NULL or short buffer");
+        return nullptr;
+    }
+    if (std::memcmp(b, kSaveMagic, 8) != 0) {
+        fail(WN_EINVAL, "wn_load: not a saved state (magic)");
+        return nullptr;
+    }
+    uint32_t n = 0, hb = 0;
+    std::memcpy(&n, b + 8, 4);
+    std::memcpy(&hb, b + 12, 4);
+    if (hb != sizeof(wn::StreamHdr) || n == 0 || (uint64_t)n * hb + 24 > buf_bytes) {
+        fail(WN_EINVAL, "wn_load: bad header (stream count or header size)");
+        return nullptr;
+    }
+    std::vector<wn::StreamHdr> h(n);
+    std::memcpy(h.data(), b + 16, (size_t)hb * n);
+    uint64_t pool_elems = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        const wn::StreamHdr &x = h[i];
+        if (!valid_pool(x.N) || !valid_passes(x.R) || x.k > x.N - 1 || x.x == 0 || x.flags != 0) {
+            fail(WN_EINVAL, "wn_load: stream " + std::to_string(i) + " has an invalid pool size, pass count, "
+                            "position or generator word");
+            return nullptr;
+        }
+        pool_elems += x.N;
+    }
+    const uint64_t need = 16 + (uint64_t)hb * n + 4 * pool_elems + 8;
+    if (buf_bytes != need) {
+        fail(WN_EINVAL, "wn_load: buffer holds " + std::to_string(buf_bytes) + " bytes, the state it describes " +
+                            std::to_string(need));
+        return nullptr;
+    }
+    uint64_t sum = 0;
+    std::memcpy(&sum, b + need - 8, 8);
+    if (sum != fnv1a64(b, need - 8)) {
+        fail(WN_EINVAL, "wn_load: checksum mismatch");
+        return nullptr;
+    }
+    const float *pools = reinterpret_cast<const float *>(b + 16 + (size_t)hb * n);
+    for (uint64_t i = 0; i < pool_elems; ++i)
+        if (!std::isfinite(pools[i])) {
+            fail(WN_EINVAL, "wn_load: non-finite pool value");
+            return nullptr;
+        }
+    std::vector<uint32_t> N(n), R(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        N[i] = h[i].N;
+        R[i] = h[i].R;
+    }
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(cuda_stream);
+    wn_stream *s = alloc_handle(n, N.data(), R.data(), cs, "wn_load");
+    if (!s) return nullptr;
+    uint64_t off = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        h[i].pool_off = off;
+        off += N[i];
+        s->k_host[i] = h[i].k;
+    }
+    cudaError_t e = cudaMemcpyAsync(s->d_hdr, h.data(), sizeof(wn::StreamHdr) * n, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_pools, pools, 4 * pool_elems, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) {
+        cuda_fail("wn_load: copy", e);
         wn_destroy(s);
         return nullptr;
     }
