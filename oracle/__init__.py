@@ -18,7 +18,10 @@ Parity status of each routine (what pins it; see the tests under ``tests/``):
                        central moment 8 nu for approximation (c)); the cubic
                        for A; exact mean of (a) and (b).
 * ``Stream``         - output moments, block sum-of-squares statistics,
-                       continuation across calls.
+                       continuation across calls; ``decimate`` (Section 5.7,
+                       every d-th pool) returns exactly blocks d-1, 2d-1, ...
+                       of the plain stream and advances the generator 2 R d
+                       draws per returned block.
 * ``philox4x32_10``  - published known-answer vectors (Random123).
 * ``boxmuller``      - special angles and radii; output moments.
 * ``gbm``            - closed-form mean and variance of the terminal price.
@@ -82,6 +85,7 @@ def lib():
                 "orc_chi2": (_dbl, [ctypes.c_int, _dbl, _dbl]),
                 "orc_create": (_p, [_u32, _u32, _u64, _u32, ctypes.c_int, ctypes.c_int]),
                 "orc_destroy": (None, [_p]),
+                "orc_set_decimate": (ctypes.c_int, [_p, _u32]),
                 "orc_generate": (None, [_p, _p, _u64]),
                 "orc_skip": (_dbl, [_p, _u64]),
                 "orc_get_pool": (None, [_p, _p]),
@@ -164,12 +168,14 @@ class Stream:
     """One Wallace stream: pool N, R passes per block, seeded by `seed`."""
 
     def __init__(self, N: int, R: int, seed: int, warmup: int = 8,
-                 chi2: str = "c", reserve: str = "previous"):
+                 chi2: str = "c", reserve: str = "previous", decimate: int = 1):
         self.N, self.R = N, R
         h = lib().orc_create(N, R, seed, warmup, CHI2[chi2], RESERVE[reserve])
         if not h:
             raise ValueError(f"invalid stream parameters N={N} R={R}")
         self._h = h
+        if lib().orc_set_decimate(h, decimate) != 0:
+            raise ValueError(f"invalid decimation {decimate}")
 
     def __del__(self):
         h = getattr(self, "_h", None)

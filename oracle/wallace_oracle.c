@@ -228,6 +228,7 @@ typedef struct {
     double g;        /* scale factor of the current block */
     uint32_t k;      /* values of the current block already returned */
     uint64_t blocks; /* blocks completed, warm-up included */
+    uint32_t decimate; /* Section 5.7: return the values of every d-th block only */
 } orc_stream;
 
 static int orc_valid(uint32_t N, uint32_t R)
@@ -309,6 +310,7 @@ orc_stream *orc_create(uint32_t N, uint32_t R, uint64_t seed, uint32_t warmup,
         s->P[i] = s->P[i] * scale;
     s->r = 0.0;
     s->g = 1.0;
+    s->decimate = 1;
     s->k = N - 1; /* no block has values left */
     for (b = 0; b < warmup; b++)
         orc_block(s);
@@ -326,6 +328,25 @@ void orc_destroy(orc_stream *s)
     free(s);
 }
 
+/* Section 5.7's remedy for finite-pool effects, "the values in every third
+ * pool": from now on a new block is the d-th of d blocks run back to back,
+ * the first d - 1 running in full (passes, scale, reserved value) but
+ * returning nothing.  d = 1 is the plain method. */
+int orc_set_decimate(orc_stream *s, uint32_t d)
+{
+    if (d < 1)
+        return -1;
+    s->decimate = d;
+    return 0;
+}
+
+static void orc_next_block(orc_stream *s)
+{
+    uint32_t t;
+    for (t = 0; t < s->decimate; t++)
+        orc_block(s);
+}
+
 /* The next `count` values of the stream's sequence, which is the
  * concatenation of the blocks' returned values; calls may cut it anywhere. */
 void orc_generate(orc_stream *s, double *out, uint64_t count)
@@ -333,7 +354,7 @@ void orc_generate(orc_stream *s, double *out, uint64_t count)
     uint64_t n = 0;
     while (n < count) {
         if (s->k == s->N - 1)
-            orc_block(s);
+            orc_next_block(s);
         while (s->k < s->N - 1 && n < count)
             out[n++] = s->blk[s->k++];
     }
@@ -347,7 +368,7 @@ double orc_skip(orc_stream *s, uint64_t count)
     double acc = 0.0;
     while (n < count) {
         if (s->k == s->N - 1)
-            orc_block(s);
+            orc_next_block(s);
         while (s->k < s->N - 1 && n < count) {
             acc += s->blk[s->k++];
             n++;

@@ -133,3 +133,28 @@ def test_invalid_parameters_rejected():
     for N, R in [(0, 1), (3, 1), (12, 1), (1024, 0)]:
         with pytest.raises(ValueError):
             oracle.Stream(N, R, seed=1)
+
+
+@pytest.mark.parametrize("N,R,d", [(16, 2, 3), (64, 1, 2), (32, 3, 5)])
+def test_pool_decimation_returns_every_dth_block(N, R, d):
+    # Section 5.7: "the values in every third pool".  The decimated stream's
+    # j-th returned block is block (j+1) d - 1 of the plain stream with the
+    # same seed (the blocks between run in full and return nothing).
+    B = 6
+    plain = oracle.Stream(N, R, 5).generate(B * d * (N - 1)).reshape(B * d, N - 1)
+    dec = oracle.Stream(N, R, 5, decimate=d).generate(B * (N - 1)).reshape(B, N - 1)
+    assert np.array_equal(dec, plain[d - 1::d])
+
+
+def test_pool_decimation_draw_count():
+    # each returned block costs d blocks of 2R draws
+    N, R, d, seed = 16, 2, 3, 9
+    s = oracle.Stream(N, R, seed, decimate=d)
+    before = s.gen_state
+    s.generate(1)
+    ref = oracle.Stream(N, R, seed)
+    assert ref.gen_state == before
+    ref.generate(d * (N - 1))
+    assert s.gen_state == ref.gen_state
+    with pytest.raises(ValueError):
+        oracle.Stream(N, R, seed, decimate=0)
