@@ -81,6 +81,39 @@ wn_stream *wn_create(uint32_t pool_N, uint32_t passes_R, uint64_t seed);
 wn_stream *wn_create_streams(uint32_t n_streams, const uint32_t *pool_N, const uint32_t *passes_R,
                              const uint64_t *seeds, uint32_t warmup_blocks, void *cuda_stream);
 
+/*
+ * Method variants (Section 5.5 and Section 5.7), for wn_create_ex.
+ *  chi2:     the chi-squared_N approximation the scale is drawn from, with x
+ *            the reserved value: WN_CHI2_C (default) A(x^2-1) +
+ *            sqrt(2(N-A^2)) x + N, A = 2 sqrt(N) sin(arcsin(1/sqrt(N))/3);
+ *            WN_CHI2_A (x + sqrt(2N-1))^2 / 2 (rann4); WN_CHI2_B
+ *            Wilson-Hilferty N ((2/(9N))^(1/2) x + 1 - 2/(9N))^3; WN_CHI2_OFF
+ *            no correction (S = N: the sum of squares never varies, the
+ *            defect Section 5.5 starts from).
+ *  reserve:  where x comes from: WN_RESERVE_PREVIOUS (default, fastnorm2:
+ *            the previous block's value held back) or WN_RESERVE_CURRENT
+ *            (fastnorm: this block's own, which Section 5.5 explains is
+ *            correlated with the block's other values).
+ *  decimate: d in [1, 255]: return the values of every d-th block only; the
+ *            d - 1 blocks between run in full and return nothing
+ *            (Section 5.7, "the values in every third pool").  1 = all.
+ */
+typedef enum { WN_CHI2_OFF = 0, WN_CHI2_A = 1, WN_CHI2_B = 2, WN_CHI2_C = 3 } wn_chi2;
+typedef enum { WN_RESERVE_PREVIOUS = 0, WN_RESERVE_CURRENT = 1 } wn_reserve;
+typedef struct {
+    uint32_t chi2;     /* wn_chi2 */
+    uint32_t reserve;  /* wn_reserve */
+    uint32_t decimate; /* 1..255 */
+} wn_options;
+
+/*
+ * wn_create_ex -- as wn_create_streams, every stream with the variants in
+ * *opt (NULL: the defaults, i.e. wn_create_streams).  Warm-up blocks are
+ * never decimated.  WN_EINVAL (NULL returned) for options out of range.
+ */
+wn_stream *wn_create_ex(uint32_t n_streams, const uint32_t *pool_N, const uint32_t *passes_R,
+                        const uint64_t *seeds, uint32_t warmup_blocks, const wn_options *opt, void *cuda_stream);
+
 /* wn_destroy -- frees the handle's device memory (synchronises the device
  * first).  NULL is accepted. */
 void wn_destroy(wn_stream *s);

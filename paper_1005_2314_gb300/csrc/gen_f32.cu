@@ -3,15 +3,16 @@
 #include "wn_gen.cuh"
 
 namespace wn {
-cudaError_t launch_generate_f32(const GenArgs &a, const LaunchCfg &c, bool full, size_t smem, cudaStream_t cs)
+cudaError_t launch_generate_f32(const GenArgs &a, const LaunchCfg &c, bool full, bool var, size_t smem,
+                               cudaStream_t cs)
 {
-    return launch_generate_t<float>(a, c, full, smem, cs);
+    return launch_generate_t<float>(a, c, full, var, smem, cs);
 }
 
-cudaError_t launch_persist_f32(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full, size_t smem,
-                               int sms, cudaStream_t cs)
+cudaError_t launch_persist_f32(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full, bool var,
+                              size_t smem, int sms, cudaStream_t cs)
 {
-    return launch_persist_t<float>(a, bq, c, full, smem, sms, cs);
+    return launch_persist_t<float>(a, bq, c, full, var, smem, sms, cs);
 }
 
 template <int QT, int MAXT, int MINB>

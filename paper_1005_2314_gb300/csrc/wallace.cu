@@ -53,13 +53,26 @@ __global__ void __launch_bounds__(32) init_kernel(StreamHdr *hdr, float *pools)
     }
     for (int o = 16; o > 0; o >>= 1) ps += __shfl_xor_sync(0xffffffffu, ps, o);
     if (lane == 0) {
+        // constants of the chi-squared approximation (Section 5.5): S/N - 1 is
+        // (A (r^2 - 1) + B r) / N for (c), for (a) (A = 1/2, B = sqrt(2N-1))
+        // and for no correction (A = B = 0); Wilson-Hilferty (b) uses
+        // A = sqrt(2/(9N)) and B = 2/(9N) in (1 + A r - B)^3 - 1
         const double nu = (double)N;
-        const double A = 2.0 * sqrt(nu) * sin(asin(1.0 / sqrt(nu)) / 3.0);
+        double A = 0.0, B = 0.0;
+        switch (var_chi2(h->variant)) {
+        case VAR_CHI2_A: A = 0.5; B = sqrt(2.0 * nu - 1.0); break;
+        case VAR_CHI2_B: B = 2.0 / (9.0 * nu); A = sqrt(B); break;
+        case VAR_CHI2_C:
+            A = 2.0 * sqrt(nu) * sin(asin(1.0 / sqrt(nu)) / 3.0);
+            B = sqrt(2.0 * (nu - A * A));
+            break;
+        default: break;
+        }
         h->x = x;
         h->w = w;
         h->r = 0.0;
         h->A = A;
-        h->B = sqrt(2.0 * (nu - A * A));
+        h->B = B;
         h->blocks = 0;
         h->scale = 1.0f;
         h->k = N - 1;
@@ -120,6 +133,9 @@ struct wn_stream {
     void *g_out = nullptr;
     int g_dtype = -1;
     std::vector<uint64_t> g_counts, g_offsets;
+    // some stream runs a method variant (wn_create_ex, wn_load): use the
+    // kernels that read StreamHdr::variant (the others compile the plain method)
+    bool var = false;
     // launch configuration chosen by wn_set_config (otherwise the default)
     bool has_cfg = false;
     wn::LaunchCfg cfg{};
@@ -199,9 +215,9 @@ wn_status launch_generate(wn_stream *s, void *out, uint64_t count, uint32_t warm
     const bool full = s->uniform_N && (uint64_t)c.threads * c.qt == s->n_max / 4;
     cudaError_t e;
     switch (dt) {
-    case WN_F32: e = wn::launch_generate_f32(a, c, full, smem, cs); break;
-    case WN_BF16: e = wn::launch_generate_bf16(a, c, full, smem, cs); break;
-    case WN_F16: e = wn::launch_generate_f16(a, c, full, smem, cs); break;
+    case WN_F32: e = wn::launch_generate_f32(a, c, full, s->var, smem, cs); break;
+    case WN_BF16: e = wn::launch_generate_bf16(a, c, full, s->var, smem, cs); break;
+    case WN_F16: e = wn::launch_generate_f16(a, c, full, s->var, smem, cs); break;
     default: return fail(WN_EINVAL, "unknown dtype");
     }
     if (e != cudaSuccess) return cuda_fail("generate launch", e);
@@ -322,9 +338,9 @@ wn_status enqueue_batch(wn_stream *s, const std::vector<Group> &groups, void *ou
         const size_t smem = wn::gen_smem_bytes(s->smem_base, g.N, g.r_max);
         cudaError_t e;
         switch (dt) {
-        case WN_F32: e = wn::launch_persist_f32(a, bq, c, full, smem, s->sms, b); break;
-        case WN_BF16: e = wn::launch_persist_bf16(a, bq, c, full, smem, s->sms, b); break;
-        default: e = wn::launch_persist_f16(a, bq, c, full, smem, s->sms, b); break;
+        case WN_F32: e = wn::launch_persist_f32(a, bq, c, full, s->var, smem, s->sms, b); break;
+        case WN_BF16: e = wn::launch_persist_bf16(a, bq, c, full, s->var, smem, s->sms, b); break;
+        default: e = wn::launch_persist_f16(a, bq, c, full, s->var, smem, s->sms, b); break;
         }
         if (e != cudaSuccess) return cuda_fail("wn_generate_batch: launch", e);
         WN_CU(cudaEventRecord(s->join[gi], b));
@@ -457,17 +473,26 @@ extern "C" {
 
 const char *wn_last_error(void) { return g_err.c_str(); }
 
-wn_stream *wn_create_streams(uint32_t n_streams, const uint32_t *pool_N, const uint32_t *passes_R,
-                             const uint64_t *seeds, uint32_t warmup_blocks, void *cuda_stream)
+wn_stream *wn_create_ex(uint32_t n_streams, const uint32_t *pool_N, const uint32_t *passes_R,
+                        const uint64_t *seeds, uint32_t warmup_blocks, const wn_options *opt, void *cuda_stream)
 {
     g_err.clear();
     if (n_streams == 0 || !pool_N || !passes_R || !seeds) {
         fail(WN_EINVAL, "wn_create_streams: empty stream set or NULL array");
         return nullptr;
     }
+    uint32_t variant = wn::VAR_CHI2_C;
+    if (opt) {
+        if (opt->chi2 > WN_CHI2_C || opt->reserve > WN_RESERVE_CURRENT || opt->decimate < 1 || opt->decimate > 255) {
+            fail(WN_EINVAL, "wn_create_ex: options out of range (chi2 0..3, reserve 0..1, decimate 1..255)");
+            return nullptr;
+        }
+        variant = opt->chi2 | (opt->reserve ? wn::VAR_RESERVE_CURRENT : 0u) | (opt->decimate << 8);
+    }
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(cuda_stream);
     wn_stream *s = alloc_handle(n_streams, pool_N, passes_R, cs, "wn_create_streams");
     if (!s) return nullptr;
+    s->var = (variant != wn::VAR_CHI2_C);
     std::vector<wn::StreamHdr> h(n_streams);
     uint64_t off = 0;
     for (uint32_t i = 0; i < n_streams; ++i) {
@@ -475,6 +500,7 @@ wn_stream *wn_create_streams(uint32_t n_streams, const uint32_t *pool_N, const u
         h[i].x = seeds[i];  // consumed by the init kernel
         h[i].N = pool_N[i];
         h[i].R = passes_R[i];
+        h[i].variant = variant;
         h[i].pool_off = off;
         off += pool_N[i];
     }
@@ -570,7 +596,8 @@ wn_stream *wn_load(const void *host_buf, uint64_t buf_bytes, void *cuda_stream)
     uint64_t pool_elems = 0;
     for (uint32_t i = 0; i < n; ++i) {
         const wn::StreamHdr &x = h[i];
-        if (!valid_pool(x.N) || !valid_passes(x.R) || x.k > x.N - 1 || x.x == 0 || x.flags != 0) {
+        if (!valid_pool(x.N) || !valid_passes(x.R) || x.k > x.N - 1 || x.x == 0 || x.flags != 0 ||
+            !wn::var_valid(x.variant)) {
             fail(WN_EINVAL, "wn_load: stream " + std::to_string(i) + " has an invalid pool size, pass count, "
                             "position or generator word");
             return nullptr;
@@ -603,6 +630,7 @@ wn_stream *wn_load(const void *host_buf, uint64_t buf_bytes, void *cuda_stream)
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(cuda_stream);
     wn_stream *s = alloc_handle(n, N.data(), R.data(), cs, "wn_load");
     if (!s) return nullptr;
+    for (uint32_t i = 0; i < n; ++i) s->var = s->var || h[i].variant != wn::VAR_CHI2_C;
     uint64_t off = 0;
     for (uint32_t i = 0; i < n; ++i) {
         h[i].pool_off = off;
@@ -618,6 +646,12 @@ wn_stream *wn_load(const void *host_buf, uint64_t buf_bytes, void *cuda_stream)
         return nullptr;
     }
     return s;
+}
+
+wn_stream *wn_create_streams(uint32_t n_streams, const uint32_t *pool_N, const uint32_t *passes_R,
+                             const uint64_t *seeds, uint32_t warmup_blocks, void *cuda_stream)
+{
+    return wn_create_ex(n_streams, pool_N, passes_R, seeds, warmup_blocks, nullptr, cuda_stream);
 }
 
 wn_stream *wn_create(uint32_t pool_N, uint32_t passes_R, uint64_t seed)
@@ -961,9 +995,9 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
                         wn::GenArgs a{s->d_hdr, s->d_pools, out, 0, 0, g.len, g.N, g.r_max, 0};
                         wn::BatchArgs bq{s->d_border + g.start, s->d_boffsets, s->d_bcounts, g.len, s->d_queue};
                         switch (dtype) {
-                        case WN_F32: e = wn::launch_persist_f32(a, bq, c, full, smem, s->sms, cs); break;
-                        case WN_BF16: e = wn::launch_persist_bf16(a, bq, c, full, smem, s->sms, cs); break;
-                        default: e = wn::launch_persist_f16(a, bq, c, full, smem, s->sms, cs); break;
+                        case WN_F32: e = wn::launch_persist_f32(a, bq, c, full, s->var, smem, s->sms, cs); break;
+                        case WN_BF16: e = wn::launch_persist_bf16(a, bq, c, full, s->var, smem, s->sms, cs); break;
+                        default: e = wn::launch_persist_f16(a, bq, c, full, s->var, smem, s->sms, cs); break;
                         }
                     }
                     if (e == cudaSuccess) e = cudaEventRecord(e1, cs);
@@ -1055,9 +1089,9 @@ wn_status wn_generate_batch_noalloc(void *out, const uint64_t *counts, const uin
         const size_t smem = wn::gen_smem_bytes(s->smem_base, N, rmax[g]);
         cudaError_t e;
         switch (dtype) {
-        case WN_F32: e = wn::launch_persist_f32(a, bq, c, full, smem, s->sms, cs); break;
-        case WN_BF16: e = wn::launch_persist_bf16(a, bq, c, full, smem, s->sms, cs); break;
-        default: e = wn::launch_persist_f16(a, bq, c, full, smem, s->sms, cs); break;
+        case WN_F32: e = wn::launch_persist_f32(a, bq, c, full, s->var, smem, s->sms, cs); break;
+        case WN_BF16: e = wn::launch_persist_bf16(a, bq, c, full, s->var, smem, s->sms, cs); break;
+        default: e = wn::launch_persist_f16(a, bq, c, full, s->var, smem, s->sms, cs); break;
         }
         if (e != cudaSuccess) return cuda_fail("wn_generate_batch_noalloc: launch", e);
     }

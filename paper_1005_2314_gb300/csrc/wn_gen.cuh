@@ -253,11 +253,13 @@ struct GbmArgs {
 //    or the reserved slot) use single stores;
 //  * EMIT_PART: the first n values of a partial last block, single stores.
 //  * EMIT_GBM: add the scaled values to the per-position sums `acc`.
-// SYNC (one pass per block) puts a barrier between the arithmetic and the
-// stores so that the control warp's scale for this block is visible.
+// nsync barriers separate the arithmetic (and the pool's stores) from the
+// scaled output, so that the control warp's scale for this block is visible:
+// one with one pass per block, two when the scale depends on this block's own
+// reserved slot (fastnorm's reserved value).
 template <int QT, bool FINAL, bool FULL, int EMIT, int A, typename OutT>
 __device__ __forceinline__ void pass_quads(uint32_t rd, uint32_t wr, uint32_t tab, uint32_t q0, uint32_t lane,
-                                           uint32_t m4, uint32_t half, uint32_t nq, float2 &part, bool sync,
+                                           uint32_t m4, uint32_t half, uint32_t nq, float2 &part, int nsync,
                                            OutT *__restrict__ ob, const float *sc_ptr, uint32_t n,
                                            float2 (&acc)[QT][2])
 {
@@ -297,7 +299,8 @@ __device__ __forceinline__ void pass_quads(uint32_t rd, uint32_t wr, uint32_t ta
         }
     }
     if (!FINAL || EMIT == EMIT_NONE) return;
-    if (sync) __syncthreads();
+    if (nsync > 0) __syncthreads();
+    if (nsync > 1) __syncthreads();
     const float sc = *sc_ptr;
     const float2 sc2 = make_float2(sc, sc);
     if (EMIT == EMIT_GBM) {
@@ -381,7 +384,7 @@ __device__ __forceinline__ void pass_quads(uint32_t rd, uint32_t wr, uint32_t ta
 // pass per block the final pass is also the first, so it waits for the scale
 // at a mid-phase barrier.
 // ---------------------------------------------------------------------------
-template <int QT, bool FULL, typename OutT, bool GBM>
+template <int QT, bool FULL, typename OutT, bool GBM, bool VAR>
 __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__restrict__ pool_g,
                                            OutT *__restrict__ out, uint64_t out_off, uint64_t count,
                                            bool store, uint32_t n_max, uint32_t r_max, const GbmArgs &gbm)
@@ -419,6 +422,11 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
     const uint64_t nb = (count - n0 + (N - 2)) / (N - 1);
     const uint64_t tail = (count - n0) % (N - 1);  // values of a partial last block (0: whole)
     const uint32_t R = h->R;
+    const uint32_t variant = VAR ? h->variant : VAR_CHI2_C;  // !VAR: the plain method, folded at compile time
+    const bool wh = var_chi2(variant) == VAR_CHI2_B;  // Wilson-Hilferty form of the scale
+    const bool late = var_current(variant);           // reserved value from this block's own pool
+    const uint32_t dec = (store || GBM) ? var_decimate(variant) : 1u;  // blocks run per returned block
+    const uint64_t nrun = nb * dec;
 
     if (control) {
         if (lane == 0) {
@@ -447,17 +455,24 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
             if (o < nwc) v += __shfl_xor_sync(0xffffffffu, v, o);
         return v;
     };
-    // Control warp: block b's scale sqrt(S / sum of squares); `pool` holds the
-    // previous block's pool (its slot N-1 is that block's reserved value,
-    // unscaled).
-    auto form_scale = [&](uint64_t b, uint32_t pool) {
+    // Control warp: block b's scale sqrt(S / sum of squares) (Section 5.5).
+    // rslot is the window address of a pool's slot N-1 (unscaled): the
+    // previous block's (fastnorm2: its reserved value times that block's
+    // scale) or, with `late`, this block's own (fastnorm: renormalised).
+    auto form_scale = [&](uint64_t b, uint32_t rslot) {
         const double ss = (b == 0) ? ctl->sumsq : sum_partials((uint32_t)((b - 1) & 1));
-        const float r = (b == 0) ? ctl->r : ctl->sc[(b - 1) & 1] * lds(pool + 4u * (N - 1));
         const float invNf = 1.0f / (float)N;  // exact: N is a power of two
-        const float delta = (float)fma(ss, (double)invNf, -1.0);              // sum/N - 1
-        const float c = __frsqrt_rn(1.0f + delta);                            // sqrt(N / sum)
-        const float u = fmaf(ctl->A, fmaf(r, r, -1.0f), ctl->B * r) * invNf;  // S/N - 1
-        const float sv = __fsqrt_rn(1.0f + u) * c;                            // sqrt(S / sum)
+        const float delta = (float)fma(ss, (double)invNf, -1.0);  // sum/N - 1
+        const float c = __frsqrt_rn(1.0f + delta);                // sqrt(N / sum)
+        const float r = late ? c * lds(rslot) : (b == 0) ? ctl->r : ctl->sc[(b - 1) & 1] * lds(rslot);
+        float u;  // S/N - 1
+        if (wh) {
+            const float d = fmaf(ctl->A, r, -ctl->B);
+            u = d * fmaf(d, d + 3.0f, 3.0f);  // (1 + d)^3 - 1
+        } else {
+            u = fmaf(ctl->A, fmaf(r, r, -1.0f), ctl->B * r) * invNf;
+        }
+        const float sv = __fsqrt_rn(1.0f + u) * c;  // sqrt(S / sum)
         __syncwarp();
         if (lane == 0) ctl->sc[b & 1] = sv;
     };
@@ -466,10 +481,13 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
     uint32_t a = (uint32_t)((out_off + n0) & 3u);  // alignment of ob within 16 bytes
     uint32_t cb = 0;                               // buffer (0 or 1) holding the current pool
     const bool one_pass = (R == 1);
+    const int nsync = late ? 2 : (one_pass ? 1 : 0);  // barriers inside the final pass
     float2 acc[QT][2];  // GBM: running sums of this thread's pool positions
 #pragma unroll
     for (int j = 0; j < QT; ++j) acc[j][0] = acc[j][1] = make_float2(0.f, 0.f);
-    for (uint64_t b = 0; b < nb; ++b) {
+    uint32_t dc = 0;  // blocks run since the last returned one (decimation)
+    uint64_t e = 0;   // blocks returned so far
+    for (uint64_t b = 0; b < nrun; ++b) {
         const uint32_t tb = tabs_s + (uint32_t)(b & 1) * r_max * (uint32_t)sizeof(PassTab);
         for (uint32_t p = 0; p < R; ++p) {
             const uint32_t rd = W0 + cb * bsz, wr = W0 + (cb ^ 1u) * bsz;
@@ -478,47 +496,54 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
                 // scale in the first phase, the next block's tables in the
                 // second (the final pass, which carries the stores): the two
                 // serial chains then each overlap a phase of compute work
-                if (p == 0) {
-                    form_scale(b, rd);
+                if (p == 0 && !late) {
+                    form_scale(b, rd + 4u * (N - 1u));
                     if (one_pass) __syncthreads();  // pairs with the final pass's mid-phase barrier
                 }
-                if (p == (one_pass ? 0u : 1u) && b + 1 < nb)
+                if (p == (one_pass ? 0u : 1u) && b + 1 < nrun)
                     make_tables(ctl, tabs + ((b + 1) & 1) * r_max, R, N, lane);
+                if (late && p + 1 == R) {  // between the final pass's pool stores and its output
+                    __syncthreads();
+                    form_scale(b, wr + 4u * (N - 1u));
+                    __syncthreads();
+                }
             } else if (p + 1 < R) {
                 float2 part;
-                pass_quads<QT, false, FULL, EMIT_NONE, 0, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part, false,
+                pass_quads<QT, false, FULL, EMIT_NONE, 0, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part, 0,
                                                                nullptr, nullptr, 0, acc);
             } else {
                 float2 part = make_float2(0.f, 0.f);
                 const float *scp = &ctl->sc[b & 1];
-                const bool whole = (b + 1 < nb) || tail == 0;
-                if (GBM) {
+                const bool emit = (dec == 1) || (dc + 1 == dec);  // decimation: a block to return
+                const bool whole = ((dec == 1 ? b : e) + 1 < nb) || tail == 0;
+                if (GBM && emit) {
                     pass_quads<QT, true, FULL, EMIT_GBM, 0, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                 one_pass, ob, scp, 0, acc);
-                } else if (!store) {
+                                                                 nsync, ob, scp, 0, acc);
+                } else if (!store || !emit) {
                     pass_quads<QT, true, FULL, EMIT_NONE, 0, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                  false, ob, scp, 0, acc);
-                    if (one_pass) __syncthreads();
+                                                                  0, ob, scp, 0, acc);
+                    if (nsync > 0) __syncthreads();
+                    if (nsync > 1) __syncthreads();
                 } else if (!whole) {
                     pass_quads<QT, true, FULL, EMIT_PART, 0, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                  one_pass, ob, scp, (uint32_t)tail, acc);
+                                                                  nsync, ob, scp, (uint32_t)tail, acc);
                 } else {
                     switch (a) {
                     case 0:
                         pass_quads<QT, true, FULL, EMIT_WHOLE, 0, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                       one_pass, ob, scp, 0, acc);
+                                                                       nsync, ob, scp, 0, acc);
                         break;
                     case 1:
                         pass_quads<QT, true, FULL, EMIT_WHOLE, 1, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                       one_pass, ob, scp, 0, acc);
+                                                                       nsync, ob, scp, 0, acc);
                         break;
                     case 2:
                         pass_quads<QT, true, FULL, EMIT_WHOLE, 2, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                       one_pass, ob, scp, 0, acc);
+                                                                       nsync, ob, scp, 0, acc);
                         break;
                     default:
                         pass_quads<QT, true, FULL, EMIT_WHOLE, 3, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                       one_pass, ob, scp, 0, acc);
+                                                                       nsync, ob, scp, 0, acc);
                         break;
                     }
                 }
@@ -529,8 +554,14 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
             cb ^= 1u;
             __syncthreads();
         }
-        ob += N - 1;
-        a = (a + N - 1) & 3u;
+        if ((dec == 1) || (dc + 1 == dec)) {  // the block was returned
+            ob += N - 1;
+            a = (a + N - 1) & 3u;
+            ++e;
+            dc = 0;
+        } else {
+            ++dc;
+        }
     }
 
     {
@@ -538,16 +569,16 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
         for (uint32_t i = tid; i < nq; i += blockDim.x) pw4[i] = lds4(W0 + cb * bsz + 16u * i);
     }
     if (control && nb > 0) {
-        const double ss = sum_partials((uint32_t)((nb - 1) & 1));
+        const double ss = sum_partials((uint32_t)((nrun - 1) & 1));
         if (lane == 0) {
-            const float sc = ctl->sc[(nb - 1) & 1];
+            const float sc = ctl->sc[(nrun - 1) & 1];
             h->x = ctl->gx;
             h->w = ctl->gw;
             h->sumsq = ss;
             h->r = (double)(sc * lds(W0 + cb * bsz + 4u * (N - 1)));
             h->scale = sc;
             h->k = tail == 0 ? N - 1 : (uint32_t)tail;
-            h->blocks += nb;
+            h->blocks += nrun;
         }
     } else if (tid == 0 && nb == 0) {
         h->k = k0 + (uint32_t)n0;
@@ -575,7 +606,7 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
 
 // FULL: every stream of the launch has exactly (blockDim.x - 32) * QT
 // quadruples, so no quadruple index needs a bounds check.
-template <int QT, int MAXT, int MINB, bool FULL, typename OutT>
+template <int QT, int MAXT, int MINB, bool FULL, typename OutT, bool VAR>
 __global__ void __launch_bounds__(MAXT, MINB) generate_kernel(GenArgs a)
 {
     StreamHdr *h = a.hdr + blockIdx.x;
@@ -584,7 +615,7 @@ __global__ void __launch_bounds__(MAXT, MINB) generate_kernel(GenArgs a)
     const uint64_t off = (uint64_t)blockIdx.x * a.out_stride;
     OutT *out = a.out ? reinterpret_cast<OutT *>(a.out) + off : nullptr;
     const GbmArgs none{};
-    run_stream<QT, FULL, OutT, false>(h, a.pools + h->pool_off, out, off, count, a.warmup_blocks == 0, a.n_max,
+    run_stream<QT, FULL, OutT, false, VAR>(h, a.pools + h->pool_off, out, off, count, a.warmup_blocks == 0, a.n_max,
                                       a.r_max, none);
 }
 
@@ -595,7 +626,8 @@ template <int QT, int MAXT, int MINB, bool FULL>
 __global__ void __launch_bounds__(MAXT, MINB) gbm_kernel(GenArgs a, GbmArgs g)
 {
     StreamHdr *h = a.hdr + blockIdx.x;
-    run_stream<QT, FULL, float, true>(h, a.pools + h->pool_off, nullptr, 0, a.count, false, a.n_max, a.r_max, g);
+    run_stream<QT, FULL, float, true, true>(h, a.pools + h->pool_off, nullptr, 0, a.count, false, a.n_max, a.r_max,
+                                            g);
 }
 
 // Work of a batch: per stream an output offset (elements from `out`) and a
@@ -612,7 +644,7 @@ struct BatchArgs {
 // the next stream from an atomic counter (longest first), returns that
 // stream's request, and claims again until the list is exhausted.  No CTA
 // waits on another.
-template <int QT, int MAXT, int MINB, bool FULL, typename OutT>
+template <int QT, int MAXT, int MINB, bool FULL, typename OutT, bool VAR>
 __global__ void __launch_bounds__(MAXT, MINB) persist_kernel(GenArgs a, BatchArgs bq)
 {
     CtlState *ctl = reinterpret_cast<CtlState *>(wn_smem + 256);
@@ -626,16 +658,19 @@ __global__ void __launch_bounds__(MAXT, MINB) persist_kernel(GenArgs a, BatchArg
         const uint32_t si = bq.order[it];
         StreamHdr *h = a.hdr + si;
         const uint64_t off = bq.offsets[si];
-        run_stream<QT, FULL, OutT, false>(h, a.pools + h->pool_off, reinterpret_cast<OutT *>(a.out) + off, off,
+        run_stream<QT, FULL, OutT, false, VAR>(h, a.pools + h->pool_off, reinterpret_cast<OutT *>(a.out) + off, off,
                                           bq.counts[si], true, a.n_max, a.r_max, none);
     }
 }
 
 template <int QT, int MAXT, int MINB, typename OutT>
-cudaError_t launch_persist_shape(const GenArgs &a, const BatchArgs &bq, uint32_t threads, bool full, size_t smem,
-                                 int sms, cudaStream_t cs)
+cudaError_t launch_persist_shape(const GenArgs &a, const BatchArgs &bq, uint32_t threads, bool full, bool var,
+                                 size_t smem, int sms, cudaStream_t cs)
 {
-    auto kern = full ? persist_kernel<QT, MAXT, MINB, true, OutT> : persist_kernel<QT, MAXT, MINB, false, OutT>;
+    auto kern = full ? (var ? persist_kernel<QT, MAXT, MINB, true, OutT, true>
+                            : persist_kernel<QT, MAXT, MINB, true, OutT, false>)
+                     : (var ? persist_kernel<QT, MAXT, MINB, false, OutT, true>
+                            : persist_kernel<QT, MAXT, MINB, false, OutT, false>);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -651,26 +686,26 @@ cudaError_t launch_persist_shape(const GenArgs &a, const BatchArgs &bq, uint32_t
 }
 
 template <typename OutT>
-cudaError_t launch_persist_t(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full, size_t smem,
-                             int sms, cudaStream_t cs)
+cudaError_t launch_persist_t(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full, bool var,
+                             size_t smem, int sms, cudaStream_t cs)
 {
     switch (c.qt * 10000 + c.maxt) {
-    case 1 * 10000 + 1024: return launch_persist_shape<1, 1024, 1, OutT>(a, bq, c.threads, full, smem, sms, cs);
-    case 2 * 10000 + 544: return launch_persist_shape<2, 544, 2, OutT>(a, bq, c.threads, full, smem, sms, cs);
-    case 4 * 10000 + 288: return launch_persist_shape<4, 288, 4, OutT>(a, bq, c.threads, full, smem, sms, cs);
-    case 8 * 10000 + 160: return launch_persist_shape<8, 160, 4, OutT>(a, bq, c.threads, full, smem, sms, cs);
-    case 8 * 10000 + 544: return launch_persist_shape<8, 544, 1, OutT>(a, bq, c.threads, full, smem, sms, cs);
-    case 16 * 10000 + 288: return launch_persist_shape<16, 288, 1, OutT>(a, bq, c.threads, full, smem, sms, cs);
+    case 1 * 10000 + 1024: return launch_persist_shape<1, 1024, 1, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
+    case 2 * 10000 + 544: return launch_persist_shape<2, 544, 2, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
+    case 4 * 10000 + 288: return launch_persist_shape<4, 288, 4, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
+    case 8 * 10000 + 160: return launch_persist_shape<8, 160, 4, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
+    case 8 * 10000 + 544: return launch_persist_shape<8, 544, 1, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
+    case 16 * 10000 + 288: return launch_persist_shape<16, 288, 1, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_persist_f32(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full, size_t smem,
-                               int sms, cudaStream_t cs);
-cudaError_t launch_persist_bf16(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full, size_t smem,
-                                int sms, cudaStream_t cs);
-cudaError_t launch_persist_f16(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full, size_t smem,
-                               int sms, cudaStream_t cs);
+cudaError_t launch_persist_f32(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full, bool var,
+                              size_t smem, int sms, cudaStream_t cs);
+cudaError_t launch_persist_bf16(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full, bool var,
+                              size_t smem, int sms, cudaStream_t cs);
+cudaError_t launch_persist_f16(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full, bool var,
+                              size_t smem, int sms, cudaStream_t cs);
 
 // Shapes of the GBM consumer {quadruples per thread, thread bound, min CTAs
 // per SM}: fewer resident CTAs than generate's, since the per-position sums
@@ -682,9 +717,12 @@ cudaError_t launch_gbm(const GenArgs &a, const GbmArgs &g, const LaunchCfg &c, b
                        cudaStream_t cs);
 
 template <int QT, int MAXT, int MINB, typename OutT>
-cudaError_t launch_shape(const GenArgs &a, uint32_t threads, bool full, size_t smem, cudaStream_t cs)
+cudaError_t launch_shape(const GenArgs &a, uint32_t threads, bool full, bool var, size_t smem, cudaStream_t cs)
 {
-    auto kern = full ? generate_kernel<QT, MAXT, MINB, true, OutT> : generate_kernel<QT, MAXT, MINB, false, OutT>;
+    auto kern = full ? (var ? generate_kernel<QT, MAXT, MINB, true, OutT, true>
+                            : generate_kernel<QT, MAXT, MINB, true, OutT, false>)
+                     : (var ? generate_kernel<QT, MAXT, MINB, false, OutT, true>
+                            : generate_kernel<QT, MAXT, MINB, false, OutT, false>);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -695,21 +733,24 @@ cudaError_t launch_shape(const GenArgs &a, uint32_t threads, bool full, size_t s
 
 // Launch of the generate kernel for one output type (defined in gen_*.cu).
 template <typename OutT>
-cudaError_t launch_generate_t(const GenArgs &a, const LaunchCfg &c, bool full, size_t smem, cudaStream_t cs)
+cudaError_t launch_generate_t(const GenArgs &a, const LaunchCfg &c, bool full, bool var, size_t smem, cudaStream_t cs)
 {
     switch (c.qt * 10000 + c.maxt) {
-    case 1 * 10000 + 1024: return launch_shape<1, 1024, 1, OutT>(a, c.threads, full, smem, cs);
-    case 2 * 10000 + 544: return launch_shape<2, 544, 2, OutT>(a, c.threads, full, smem, cs);
-    case 4 * 10000 + 288: return launch_shape<4, 288, 4, OutT>(a, c.threads, full, smem, cs);
-    case 8 * 10000 + 160: return launch_shape<8, 160, 4, OutT>(a, c.threads, full, smem, cs);
-    case 8 * 10000 + 544: return launch_shape<8, 544, 1, OutT>(a, c.threads, full, smem, cs);
-    case 16 * 10000 + 288: return launch_shape<16, 288, 1, OutT>(a, c.threads, full, smem, cs);
+    case 1 * 10000 + 1024: return launch_shape<1, 1024, 1, OutT>(a, c.threads, full, var, smem, cs);
+    case 2 * 10000 + 544: return launch_shape<2, 544, 2, OutT>(a, c.threads, full, var, smem, cs);
+    case 4 * 10000 + 288: return launch_shape<4, 288, 4, OutT>(a, c.threads, full, var, smem, cs);
+    case 8 * 10000 + 160: return launch_shape<8, 160, 4, OutT>(a, c.threads, full, var, smem, cs);
+    case 8 * 10000 + 544: return launch_shape<8, 544, 1, OutT>(a, c.threads, full, var, smem, cs);
+    case 16 * 10000 + 288: return launch_shape<16, 288, 1, OutT>(a, c.threads, full, var, smem, cs);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_generate_f32(const GenArgs &a, const LaunchCfg &c, bool full, size_t smem, cudaStream_t cs);
-cudaError_t launch_generate_bf16(const GenArgs &a, const LaunchCfg &c, bool full, size_t smem, cudaStream_t cs);
-cudaError_t launch_generate_f16(const GenArgs &a, const LaunchCfg &c, bool full, size_t smem, cudaStream_t cs);
+cudaError_t launch_generate_f32(const GenArgs &a, const LaunchCfg &c, bool full, bool var, size_t smem,
+                               cudaStream_t cs);
+cudaError_t launch_generate_bf16(const GenArgs &a, const LaunchCfg &c, bool full, bool var, size_t smem,
+                               cudaStream_t cs);
+cudaError_t launch_generate_f16(const GenArgs &a, const LaunchCfg &c, bool full, bool var, size_t smem,
+                               cudaStream_t cs);
 
 }  // namespace wn

@@ -22,10 +22,10 @@ def fnv1a64(b: bytes) -> int:
 
 
 def state(Ns=(8, 16), Rs=(2, 1), k=None, x=12345, flags=0, pool=None, magic=b"WNSTATE1", hdr_bytes=96,
-          bad_sum=False, extra=b""):
+          bad_sum=False, extra=b"", variant=3):
     body = magic + struct.pack("<II", len(Ns), hdr_bytes)
     for i, (N, R) in enumerate(zip(Ns, Rs)):
-        body += HDR.pack(x, 7, 0.25, 0.66, 1.0, 0, 3, 1.0, (N - 1) if k is None else k, N, R, flags, 0,
+        body += HDR.pack(x, 7, 0.25, 0.66, 1.0, 0, 3, 1.0, (N - 1) if k is None else k, N, R, flags, variant,
                          float(N), 0)
     for N in Ns:
         p = np.linspace(-1, 1, N, dtype=np.float32) if pool is None else np.full(N, pool, np.float32)
@@ -57,13 +57,14 @@ def test_header_size_is_96():
     (state(k=8), "invalid pool size"),
     (state(x=0), "invalid pool size"),
     (state(flags=1), "invalid pool size"),
+    (state(variant=0x10003), "invalid pool size"),
     (state(bad_sum=True), "checksum"),
     (state(extra=b"\0"), "buffer holds"),
     (state()[:-1], "buffer holds"),
     (state(pool=np.nan), "non-finite"),
     (state(pool=np.inf), "non-finite"),
 ], ids=["empty", "magic", "header-size", "N-not-pow2", "N-too-big", "R-zero", "R-too-big", "k-past-block",
-        "x-zero", "flag-set", "checksum", "trailing-byte", "truncated", "nan-pool", "inf-pool"])
+        "x-zero", "flag-set", "variant-bits", "checksum", "trailing-byte", "truncated", "nan-pool", "inf-pool"])
 def test_load_rejects_corrupt_state(lib, buf, why):
     with pytest.raises(lib.WnError, match=why):
         lib.wn_load(buf, 0)  # an explicit (legacy default) stream: no torch CUDA call
