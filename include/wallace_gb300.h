@@ -96,7 +96,7 @@ wn_stream *wn_create_streams(uint32_t n_streams, const uint32_t *pool_N, const u
  *            correlated with the block's other values).
  *  decimate: d in [1, 255]: return the values of every d-th block only; the
  *            d - 1 blocks between run in full and return nothing
- *            (Section 5.7, "the values in every third pool").  1 = all.
+ *            (Section 5.7: keep one pool in d).  1 = all.
  */
 typedef enum { WN_CHI2_OFF = 0, WN_CHI2_A = 1, WN_CHI2_B = 2, WN_CHI2_C = 3 } wn_chi2;
 typedef enum { WN_RESERVE_PREVIOUS = 0, WN_RESERVE_CURRENT = 1 } wn_reserve;

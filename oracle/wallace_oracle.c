@@ -328,8 +328,8 @@ void orc_destroy(orc_stream *s)
     free(s);
 }
 
-/* Section 5.7's remedy for finite-pool effects, "the values in every third
- * pool": from now on a new block is the d-th of d blocks run back to back,
+/* Section 5.7's remedy for finite-pool effects, keeping only one pool in
+ * three (here one in d): from now on a new block is the d-th of d blocks run back to back,
  * the first d - 1 running in full (passes, scale, reserved value) but
  * returning nothing.  d = 1 is the plain method. */
 int orc_set_decimate(orc_stream *s, uint32_t d)

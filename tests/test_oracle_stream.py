@@ -137,7 +137,7 @@ def test_invalid_parameters_rejected():
 
 @pytest.mark.parametrize("N,R,d", [(16, 2, 3), (64, 1, 2), (32, 3, 5)])
 def test_pool_decimation_returns_every_dth_block(N, R, d):
-    # Section 5.7: "the values in every third pool".  The decimated stream's
+    # Section 5.7's remedy of keeping only one pool in three.  The decimated stream's
     # j-th returned block is block (j+1) d - 1 of the plain stream with the
     # same seed (the blocks between run in full and return nothing).
     B = 6
