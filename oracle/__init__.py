@@ -14,6 +14,11 @@ Parity status of each routine (what pins it; see the tests under ``tests/``):
 * ``pass_``          - printed matrix A_1 (Section 5.3) up to row order and
                        signs; hand-worked N=4 example; involution; sum of
                        squares preserved; brute-force mixing reach.
+* ``pass_rot``       - the rotation form (Section 5.3, rann4): hand-worked
+                       N=4 example (t = 1/2: c = 3/5, s = 4/5); c^2+s^2 = 1;
+                       sum of squares preserved; exact inverse; each output
+                       a combination of exactly two inputs; mixing reach
+                       log2 N passes; t's range and symmetry.
 * ``chi2``           - closed-form moments (E S = nu, Var S = 2 nu, third
                        central moment 8 nu for approximation (c)); the cubic
                        for A; exact mean of (a) and (b).
@@ -48,6 +53,7 @@ _lib = None
 
 CHI2 = {"off": 0, "a": 1, "b": 2, "c": 3}
 RESERVE = {"previous": 0, "current": 1}
+UPDATE = {"quad": 0, "rotation": 1}
 
 _u64 = ctypes.c_uint64
 _u32 = ctypes.c_uint32
@@ -86,6 +92,10 @@ def lib():
                 "orc_create": (_p, [_u32, _u32, _u64, _u32, ctypes.c_int, ctypes.c_int]),
                 "orc_destroy": (None, [_p]),
                 "orc_set_decimate": (ctypes.c_int, [_p, _u32]),
+                "orc_set_update": (ctypes.c_int, [_p, ctypes.c_int]),
+                "orc_rot_t": (_dbl, [_u64]),
+                "orc_pass_rot": (None, [_u32, _p, _p, _u64, _u64]),
+                "orc_pass_rot_inverse": (None, [_u32, _p, _p, _u64, _u64]),
                 "orc_generate": (None, [_p, _p, _u64]),
                 "orc_skip": (_dbl, [_p, _u64]),
                 "orc_get_pool": (None, [_p, _p]),
@@ -140,6 +150,26 @@ def pass_read_slots(N: int, w_a: int) -> np.ndarray:
     return out
 
 
+def rot_t(w_t: int) -> float:
+    """The rotation parameter t = tan(theta/2) a rotation pass takes from its draw."""
+    return lib().orc_rot_t(w_t)
+
+
+def pass_rot(N: int, P: np.ndarray, w_a: int, w_t: int) -> np.ndarray:
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    assert P.shape == (N,)
+    out = np.empty(N, dtype=np.float64)
+    lib().orc_pass_rot(N, _ptr(P), _ptr(out), w_a, w_t)
+    return out
+
+
+def pass_rot_inverse(N: int, Pn: np.ndarray, w_a: int, w_t: int) -> np.ndarray:
+    Pn = np.ascontiguousarray(Pn, dtype=np.float64)
+    out = np.empty(N, dtype=np.float64)
+    lib().orc_pass_rot_inverse(N, _ptr(Pn), _ptr(out), w_a, w_t)
+    return out
+
+
 def pass_(N: int, P: np.ndarray, w_a: int, w_s: int) -> np.ndarray:
     P = np.ascontiguousarray(P, dtype=np.float64)
     assert P.shape == (N,)
@@ -168,7 +198,7 @@ class Stream:
     """One Wallace stream: pool N, R passes per block, seeded by `seed`."""
 
     def __init__(self, N: int, R: int, seed: int, warmup: int = 8,
-                 chi2: str = "c", reserve: str = "previous", decimate: int = 1):
+                 chi2: str = "c", reserve: str = "previous", decimate: int = 1, update: str = "quad"):
         self.N, self.R = N, R
         h = lib().orc_create(N, R, seed, warmup, CHI2[chi2], RESERVE[reserve])
         if not h:
@@ -176,6 +206,8 @@ class Stream:
         self._h = h
         if lib().orc_set_decimate(h, decimate) != 0:
             raise ValueError(f"invalid decimation {decimate}")
+        if update not in UPDATE or lib().orc_set_update(h, UPDATE[update]) != 0:
+            raise ValueError(f"invalid update {update}")
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -178,6 +178,50 @@ void orc_pass_inverse(uint32_t N, const double *Pn, double *P, uint64_t w_a, uin
 }
 
 /* ---------------------------------------------------------------- */
+/* The plane-rotation form (rann4, Section 5.3): one rotation        */
+/* R(theta) = [c s; -s c] per pass, c = (1-t^2)/(1+t^2),              */
+/* s = 2t/(1+t^2), t = tan(theta/2) drawn for the pass (theta itself  */
+/* is never formed), applied to pairs gathered through the pass's     */
+/* affine permutation (Section 5.4).                                  */
+/* ---------------------------------------------------------------- */
+
+/* t in (-1, 1) from the top 24 bits u of the pass's second draw:
+ * t = (2u + 1) / 2^24 - 1, exact in FP64 (and in FP32). */
+double orc_rot_t(uint64_t w_t)
+{
+    uint64_t u = w_t >> 40;
+    return (double)(2 * u + 1) / 16777216.0 - 1.0;
+}
+
+/* Pair j (0 <= j < N/2) takes a = P[pi(j)], b = P[pi(j + N/2)] and writes
+ * (c a + s b, -s a + c b) to slots 2j, 2j+1 (the transposed write). */
+void orc_pass_rot(uint32_t N, const double *P, double *Pn, uint64_t w_a, uint64_t w_t)
+{
+    uint64_t alpha = orc_alpha(N, w_a), gamma = orc_gamma(N, w_a);
+    double t = orc_rot_t(w_t), c = (1.0 - t * t) / (1.0 + t * t), s = 2.0 * t / (1.0 + t * t);
+    uint32_t j;
+    for (j = 0; j < N / 2; j++) {
+        double a = P[(alpha * j + gamma) % N];
+        double b = P[(alpha * (j + N / 2) + gamma) % N];
+        Pn[2 * j] = c * a + s * b;
+        Pn[2 * j + 1] = -s * a + c * b;
+    }
+}
+
+/* The inverse of orc_pass_rot (the transposed rotation, gathered back). */
+void orc_pass_rot_inverse(uint32_t N, const double *Pn, double *P, uint64_t w_a, uint64_t w_t)
+{
+    uint64_t alpha = orc_alpha(N, w_a), gamma = orc_gamma(N, w_a);
+    double t = orc_rot_t(w_t), c = (1.0 - t * t) / (1.0 + t * t), s = 2.0 * t / (1.0 + t * t);
+    uint32_t j;
+    for (j = 0; j < N / 2; j++) {
+        double y0 = Pn[2 * j], y1 = Pn[2 * j + 1];
+        P[(alpha * j + gamma) % N] = c * y0 - s * y1;
+        P[(alpha * (j + N / 2) + gamma) % N] = s * y0 + c * y1;
+    }
+}
+
+/* ---------------------------------------------------------------- */
 /* Chi-squared approximations (Section 5.5).                        */
 /* ---------------------------------------------------------------- */
 
@@ -229,6 +273,7 @@ typedef struct {
     uint32_t k;      /* values of the current block already returned */
     uint64_t blocks; /* blocks completed, warm-up included */
     uint32_t decimate; /* Section 5.7: return the values of every d-th block only */
+    int update;        /* 0: the 4x4 form (fastnorm); 1: plane rotations (rann4) */
 } orc_stream;
 
 static int orc_valid(uint32_t N, uint32_t R)
@@ -245,7 +290,10 @@ static void orc_block(orc_stream *s)
         uint64_t w_a = orc_u64gen_next(&s->gen);
         uint64_t w_s = orc_u64gen_next(&s->gen);
         double *t;
-        orc_pass(N, s->P, s->tmp, w_a, w_s);
+        if (s->update)
+            orc_pass_rot(N, s->P, s->tmp, w_a, w_s);
+        else
+            orc_pass(N, s->P, s->tmp, w_a, w_s);
         t = s->P;
         s->P = s->tmp;
         s->tmp = t;
@@ -337,6 +385,16 @@ int orc_set_decimate(orc_stream *s, uint32_t d)
     if (d < 1)
         return -1;
     s->decimate = d;
+    return 0;
+}
+
+/* Section 5.3's alternative update: 0 keeps the 4x4 form, 1 selects plane
+ * rotations (the pass's second draw gives t instead of the signs). */
+int orc_set_update(orc_stream *s, int update)
+{
+    if (update != 0 && update != 1)
+        return -1;
+    s->update = update;
     return 0;
 }
 
