@@ -92,7 +92,7 @@ def lib():
                 "orc_create": (_p, [_u32, _u32, _u64, _u32, ctypes.c_int, ctypes.c_int]),
                 "orc_destroy": (None, [_p]),
                 "orc_set_decimate": (ctypes.c_int, [_p, _u32]),
-                "orc_set_update": (ctypes.c_int, [_p, ctypes.c_int]),
+                "orc_create_update": (_p, [_u32, _u32, _u64, _u32, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
                 "orc_rot_t": (_dbl, [_u64]),
                 "orc_pass_rot": (None, [_u32, _p, _p, _u64, _u64]),
                 "orc_pass_rot_inverse": (None, [_u32, _p, _p, _u64, _u64]),
@@ -200,14 +200,14 @@ class Stream:
     def __init__(self, N: int, R: int, seed: int, warmup: int = 8,
                  chi2: str = "c", reserve: str = "previous", decimate: int = 1, update: str = "quad"):
         self.N, self.R = N, R
-        h = lib().orc_create(N, R, seed, warmup, CHI2[chi2], RESERVE[reserve])
+        if update not in UPDATE:
+            raise ValueError(f"invalid update {update}")
+        h = lib().orc_create_update(N, R, seed, warmup, CHI2[chi2], RESERVE[reserve], UPDATE[update])
         if not h:
             raise ValueError(f"invalid stream parameters N={N} R={R}")
         self._h = h
         if lib().orc_set_decimate(h, decimate) != 0:
             raise ValueError(f"invalid decimation {decimate}")
-        if update not in UPDATE or lib().orc_set_update(h, UPDATE[update]) != 0:
-            raise ValueError(f"invalid update {update}")
 
     def __del__(self):
         h = getattr(self, "_h", None)

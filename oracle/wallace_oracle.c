@@ -317,13 +317,15 @@ static void orc_block(orc_stream *s)
     s->blocks++;
 }
 
-orc_stream *orc_create(uint32_t N, uint32_t R, uint64_t seed, uint32_t warmup,
-                       int chi2_kind, int reserve_mode)
+/* A stream whose passes (warm-up included) use the 4x4 update (update 0)
+ * or plane rotations (update 1, Section 5.3). */
+orc_stream *orc_create_update(uint32_t N, uint32_t R, uint64_t seed, uint32_t warmup,
+                              int chi2_kind, int reserve_mode, int update)
 {
     orc_stream *s;
     uint32_t i, b, f;
     double sumsq, scale;
-    if (!orc_valid(N, R))
+    if (!orc_valid(N, R) || (update != 0 && update != 1))
         return NULL;
     s = (orc_stream *)calloc(1, sizeof(*s));
     if (!s)
@@ -359,11 +361,18 @@ orc_stream *orc_create(uint32_t N, uint32_t R, uint64_t seed, uint32_t warmup,
     s->r = 0.0;
     s->g = 1.0;
     s->decimate = 1;
+    s->update = update;
     s->k = N - 1; /* no block has values left */
     for (b = 0; b < warmup; b++)
         orc_block(s);
     s->k = N - 1;
     return s;
+}
+
+orc_stream *orc_create(uint32_t N, uint32_t R, uint64_t seed, uint32_t warmup,
+                       int chi2_kind, int reserve_mode)
+{
+    return orc_create_update(N, R, seed, warmup, chi2_kind, reserve_mode, 0);
 }
 
 void orc_destroy(orc_stream *s)
@@ -385,16 +394,6 @@ int orc_set_decimate(orc_stream *s, uint32_t d)
     if (d < 1)
         return -1;
     s->decimate = d;
-    return 0;
-}
-
-/* Section 5.3's alternative update: 0 keeps the 4x4 form, 1 selects plane
- * rotations (the pass's second draw gives t instead of the signs). */
-int orc_set_update(orc_stream *s, int update)
-{
-    if (update != 0 && update != 1)
-        return -1;
-    s->update = update;
     return 0;
 }
 

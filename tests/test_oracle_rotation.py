@@ -86,3 +86,19 @@ def test_rotation_stream_moments_and_continuation():
     assert np.array_equal(parts, oracle.Stream(N, R, 7, update="rotation").generate(parts.size))
     with pytest.raises(ValueError):
         oracle.Stream(N, R, 7, update="other")
+
+
+def test_warmup_blocks_use_the_rotation_form():
+    # the initial pool is the same for both updates; a warm-up block then
+    # applies R rotation passes (draws after the N used by the initial pool)
+    # and renormalises to sum of squares N
+    N, R, seed = 64, 3, 11
+    P0 = oracle.Stream(N, R, seed, warmup=0, update="rotation").pool
+    assert np.array_equal(P0, oracle.Stream(N, R, seed, warmup=0).pool)
+    d = oracle.draws(seed, N + 2 * R)
+    P = P0
+    for p in range(R):
+        P = oracle.pass_rot(N, P, int(d[N + 2 * p]), int(d[N + 2 * p + 1]))
+    P = P * math.sqrt(N / np.dot(P, P))
+    assert np.allclose(oracle.Stream(N, R, seed, warmup=1, update="rotation").pool, P, rtol=0, atol=1e-13)
+    assert not np.allclose(oracle.Stream(N, R, seed, warmup=1).pool, P, atol=1e-3)
