@@ -97,13 +97,22 @@ wn_stream *wn_create_streams(uint32_t n_streams, const uint32_t *pool_N, const u
  *  decimate: d in [1, 255]: return the values of every d-th block only; the
  *            d - 1 blocks between run in full and return nothing
  *            (Section 5.7: keep one pool in d).  1 = all.
+ *  update:   WN_UPDATE_QUAD (default) the random-signed 4x4 update of
+ *            fastnorm; WN_UPDATE_ROTATION rann4's plane rotations (Section
+ *            5.3): each pass draws t = tan(theta/2) in (-1, 1) from the top
+ *            24 bits u of its second draw, t = (2u+1)/2^24 - 1, and rotates
+ *            the pairs (P[pi(j)], P[pi(j + N/2)]), pi the pass's affine
+ *            permutation (Section 5.4), by c = (1-t^2)/(1+t^2),
+ *            s = 2t/(1+t^2), writing them to slots 2j, 2j+1.
  */
 typedef enum { WN_CHI2_OFF = 0, WN_CHI2_A = 1, WN_CHI2_B = 2, WN_CHI2_C = 3 } wn_chi2;
 typedef enum { WN_RESERVE_PREVIOUS = 0, WN_RESERVE_CURRENT = 1 } wn_reserve;
+typedef enum { WN_UPDATE_QUAD = 0, WN_UPDATE_ROTATION = 1 } wn_update;
 typedef struct {
     uint32_t chi2;     /* wn_chi2 */
     uint32_t reserve;  /* wn_reserve */
     uint32_t decimate; /* 1..255 */
+    uint32_t update;   /* wn_update */
 } wn_options;
 
 /*

@@ -22,7 +22,7 @@ from . import build as _build
 
 __all__ = [
     "WN_F32", "WN_BF16", "WN_F16", "WnError",
-    "wn_create", "wn_create_streams", "wn_create_ex", "WN_CHI2", "WN_RESERVE", "wn_destroy", "wn_generate", "wn_generate_ex",
+    "wn_create", "wn_create_streams", "wn_create_ex", "WN_CHI2", "WN_RESERVE", "WN_UPDATE", "wn_destroy", "wn_generate", "wn_generate_ex",
     "wn_generate_host",
     "wn_set_cuda_stream", "wn_set_config", "wn_get_config", "wn_autotune", "wn_gbm", "wn_generate_batch",
     "wn_autotune_batch", "wn_generate_batch_noalloc", "wn_num_streams", "wn_get_pool", "wn_get_state",
@@ -179,23 +179,25 @@ def wn_create_streams(pool_N, passes_R, seeds, warmup_blocks: int = 8, cuda_stre
 
 
 class _Options(ctypes.Structure):
-    _fields_ = [("chi2", _u32), ("reserve", _u32), ("decimate", _u32)]
+    _fields_ = [("chi2", _u32), ("reserve", _u32), ("decimate", _u32), ("update", _u32)]
 
 
 WN_CHI2 = {"off": 0, "a": 1, "b": 2, "c": 3}
 WN_RESERVE = {"previous": 0, "current": 1}
+WN_UPDATE = {"quad": 0, "rotation": 1}
 
 
 def wn_create_ex(pool_N, passes_R, seeds, warmup_blocks: int = 8, chi2: str = "c", reserve: str = "previous",
-                 decimate: int = 1, cuda_stream=None) -> Handle:
-    """wn_create_streams with the method variants of wn_options (names as in WN_CHI2 / WN_RESERVE)."""
-    if chi2 not in WN_CHI2 or reserve not in WN_RESERVE:
-        raise ValueError(f"chi2 must be one of {list(WN_CHI2)} and reserve one of {list(WN_RESERVE)}")
+                 decimate: int = 1, update: str = "quad", cuda_stream=None) -> Handle:
+    """wn_create_streams with the method variants of wn_options (names as in WN_CHI2 / WN_RESERVE / WN_UPDATE)."""
+    if chi2 not in WN_CHI2 or reserve not in WN_RESERVE or update not in WN_UPDATE:
+        raise ValueError(f"chi2 must be one of {list(WN_CHI2)}, reserve one of {list(WN_RESERVE)}, "
+                         f"update one of {list(WN_UPDATE)}")
     seeds = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
     n = seeds.size
     N = np.ascontiguousarray(np.broadcast_to(np.asarray(pool_N, dtype=np.uint32), (n,)))
     R = np.ascontiguousarray(np.broadcast_to(np.asarray(passes_R, dtype=np.uint32), (n,)))
-    opt = _Options(WN_CHI2[chi2], WN_RESERVE[reserve], int(decimate))
+    opt = _Options(WN_CHI2[chi2], WN_RESERVE[reserve], int(decimate), WN_UPDATE[update])
     h = _L().wn_create_ex(n, N.ctypes.data, R.ctypes.data, seeds.ctypes.data, warmup_blocks, ctypes.byref(opt),
                           _stream_ptr(cuda_stream))
     if not h:

@@ -1,0 +1,11 @@
+// persist_f32.cu -- the persistent batch kernel instantiated for float output (a
+// translation unit of its own, so it compiles in parallel with the others).
+#include "wn_gen.cuh"
+
+namespace wn {
+cudaError_t launch_persist_f32(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full, bool var,
+                              size_t smem, int sms, cudaStream_t cs)
+{
+    return launch_persist_t<float>(a, bq, c, full, var, smem, sms, cs);
+}
+}  // namespace wn

@@ -483,11 +483,13 @@ wn_stream *wn_create_ex(uint32_t n_streams, const uint32_t *pool_N, const uint32
     }
     uint32_t variant = wn::VAR_CHI2_C;
     if (opt) {
-        if (opt->chi2 > WN_CHI2_C || opt->reserve > WN_RESERVE_CURRENT || opt->decimate < 1 || opt->decimate > 255) {
-            fail(WN_EINVAL, "wn_create_ex: options out of range (chi2 0..3, reserve 0..1, decimate 1..255)");
+        if (opt->chi2 > WN_CHI2_C || opt->reserve > WN_RESERVE_CURRENT || opt->decimate < 1 || opt->decimate > 255 ||
+            opt->update > WN_UPDATE_ROTATION) {
+            fail(WN_EINVAL, "wn_create_ex: options out of range (chi2 0..3, reserve 0..1, decimate 1..255, update 0..1)");
             return nullptr;
         }
-        variant = opt->chi2 | (opt->reserve ? wn::VAR_RESERVE_CURRENT : 0u) | (opt->decimate << 8);
+        variant = opt->chi2 | (opt->reserve ? wn::VAR_RESERVE_CURRENT : 0u) |
+                  (opt->update ? wn::VAR_ROTATION : 0u) | (opt->decimate << 8);
     }
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(cuda_stream);
     wn_stream *s = alloc_handle(n_streams, pool_N, passes_R, cs, "wn_create_streams");

@@ -30,7 +30,8 @@ struct __align__(16) StreamHdr {
     uint32_t R;        // passes per block
     uint32_t flags;    // nonzero: a launch could not run this stream (bit 0: shared-memory layout)
     uint32_t variant;  // bits 0-1 chi-squared approximation (VAR_CHI2_*), bit 2 reserved value from the
-                       // current pool (fastnorm), bits 8-15 pool decimation d (0 and 1: none)
+                       // current pool (fastnorm), bit 3 plane rotations instead of the 4x4 update
+                       // (rann4), bits 8-15 pool decimation d (0 and 1: none)
     double sumsq;      // sum of squares of the stored pool, as the generate kernel forms it
     uint64_t pad2_;
 };
@@ -38,11 +39,12 @@ static_assert(sizeof(StreamHdr) == 96, "StreamHdr layout");
 
 // StreamHdr::variant (Section 5.5's approximations and reserved value; Section 5.7's decimation)
 constexpr uint32_t VAR_CHI2_OFF = 0, VAR_CHI2_A = 1, VAR_CHI2_B = 2, VAR_CHI2_C = 3;
-constexpr uint32_t VAR_RESERVE_CURRENT = 4u;
+constexpr uint32_t VAR_RESERVE_CURRENT = 4u, VAR_ROTATION = 8u;
 __host__ __device__ inline uint32_t var_chi2(uint32_t v) { return v & 3u; }
 __host__ __device__ inline bool var_current(uint32_t v) { return (v & VAR_RESERVE_CURRENT) != 0; }
 __host__ __device__ inline uint32_t var_decimate(uint32_t v) { return ((v >> 8) & 0xFFu) > 1u ? (v >> 8) & 0xFFu : 1u; }
-__host__ __device__ inline bool var_valid(uint32_t v) { return (v & ~0xFF07u) == 0; }
+__host__ __device__ inline bool var_rotation(uint32_t v) { return (v & VAR_ROTATION) != 0; }
+__host__ __device__ inline bool var_valid(uint32_t v) { return (v & ~0xFF0Fu) == 0; }
 
 constexpr uint64_t kGoldenGamma = 0x9E3779B97F4A7C15ull;
 constexpr uint64_t kWeyl = 0x61C8864680B583EBull;  // 2^64 - kGoldenGamma, odd

@@ -166,7 +166,14 @@ __device__ __forceinline__ float neg_sign_one(uint32_t bit) { return __uint_as_f
 
 // Control warp: draw the R passes' (w_a, w_s) of the coming block from the
 // stream generator, in the order the method draws them, and tabulate them.
-__device__ __forceinline__ void make_tables(CtlState *ctl, PassTab *tab, uint32_t R, uint32_t N, uint32_t lane)
+// With `rot` (the plane-rotation form of Section 5.3) the second draw gives
+// t = (2u + 1)/2^24 - 1, u its top 24 bits, and the pass rotates pairs by
+// c = (1 - t^2)/(1 + t^2), s = 2t/(1 + t^2) (FP64, rounded to FP32 once); the
+// table then describes quadruple q as the pairs 2q and 2q+1: element 0 at
+// 8 alpha q + 4 gamma, element 2 its partner N/2 away, elements 1 and 3 the
+// next pair (offset 4 alpha), and every sgn entry holds (c, s, c, s).
+__device__ __forceinline__ void make_tables(CtlState *ctl, PassTab *tab, uint32_t R, uint32_t N, uint32_t lane,
+                                            bool rot)
 {
     uint64_t gx = ctl->gx, gw = ctl->gw;
     for (uint32_t p = 0; p < R; ++p) {
@@ -174,6 +181,20 @@ __device__ __forceinline__ void make_tables(CtlState *ctl, PassTab *tab, uint32_
         const uint64_t ws = draw(gx, gw);
         const uint32_t alpha = ((uint32_t)(wa >> 32) & (N - 1)) | 1u;
         const uint32_t gamma = (uint32_t)wa & (N - 1);
+        if (rot) {
+            if (lane < 16) {
+                const double t = (double)(2u * (uint32_t)(ws >> 40) + 1u) * (1.0 / 16777216.0) - 1.0;
+                const double d = 1.0 + t * t;
+                const float c = (float)((1.0 - t * t) / d), sn = (float)(2.0 * t / d);
+                tab[p].sgn[lane] = make_float4(c, sn, c, sn);
+            } else if (lane == 16) {
+                tab[p].a4 = 8u * alpha;
+                tab[p].g4 = 4u * gamma;
+                tab[p].d1 = 4u * alpha;
+                tab[p].dq = 256u * alpha;
+            }
+            continue;
+        }
         if (lane < 16) {
             const uint32_t nib = (uint32_t)(ws >> (4u * lane)) & 15u;
             tab[p].sgn[lane] = make_float4(neg_sign_one(nib & 1u), neg_sign_one((nib >> 1) & 1u),
@@ -257,7 +278,7 @@ struct GbmArgs {
 // scaled output, so that the control warp's scale for this block is visible:
 // one with one pass per block, two when the scale depends on this block's own
 // reserved slot (fastnorm's reserved value).
-template <int QT, bool FINAL, bool FULL, int EMIT, int A, typename OutT>
+template <int QT, bool FINAL, bool FULL, int EMIT, int A, typename OutT, bool ROT>
 __device__ __forceinline__ void pass_quads(uint32_t rd, uint32_t wr, uint32_t tab, uint32_t q0, uint32_t lane,
                                            uint32_t m4, uint32_t half, uint32_t nq, float2 &part, int nsync,
                                            OutT *__restrict__ ob, const float *sc_ptr, uint32_t n,
@@ -287,12 +308,18 @@ __device__ __forceinline__ void pass_quads(uint32_t rd, uint32_t wr, uint32_t ta
 #pragma unroll
     for (int j = 0; j < QT; ++j) {
         const uint32_t q = q0 + 32u * j;
-        const float2 a01 = make_float2(a[j][0], a[j][1]), a23 = make_float2(a[j][2], a[j][3]);
-        const float2 s2 = fadd2(a01, a23);
-        const float sum = s2.x + s2.y;
-        const float2 SS = make_float2(sum, sum);
-        y[j][0] = ffma2(m01, a01, fmul2(h01, SS));
-        y[j][1] = ffma2(m23, a23, fmul2(h23, SS));
+        if (ROT) {  // pairs (a0, a2) and (a1, a3) rotated by (c, s) = m01
+            const float c = m01.x, sn = m01.y;
+            y[j][0] = make_float2(fmaf(c, a[j][0], sn * a[j][2]), fmaf(c, a[j][2], -sn * a[j][0]));
+            y[j][1] = make_float2(fmaf(c, a[j][1], sn * a[j][3]), fmaf(c, a[j][3], -sn * a[j][1]));
+        } else {
+            const float2 a01 = make_float2(a[j][0], a[j][1]), a23 = make_float2(a[j][2], a[j][3]);
+            const float2 s2 = fadd2(a01, a23);
+            const float sum = s2.x + s2.y;
+            const float2 SS = make_float2(sum, sum);
+            y[j][0] = ffma2(m01, a01, fmul2(h01, SS));
+            y[j][1] = ffma2(m23, a23, fmul2(h23, SS));
+        }
         if (FULL || q < nq) {
             sts4(wr + 16u * q, y[j][0], y[j][1]);
             if (FINAL) part = ffma2(y[j][0], y[j][0], ffma2(y[j][1], y[j][1], part));
@@ -384,7 +411,7 @@ __device__ __forceinline__ void pass_quads(uint32_t rd, uint32_t wr, uint32_t ta
 // pass per block the final pass is also the first, so it waits for the scale
 // at a mid-phase barrier.
 // ---------------------------------------------------------------------------
-template <int QT, bool FULL, typename OutT, bool GBM, bool VAR>
+template <int QT, bool FULL, typename OutT, bool GBM, bool VAR, bool ROT>
 __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__restrict__ pool_g,
                                            OutT *__restrict__ out, uint64_t out_off, uint64_t count,
                                            bool store, uint32_t n_max, uint32_t r_max, const GbmArgs &gbm)
@@ -439,7 +466,7 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
             ctl->sc[1] = sc_prev;
         }
         __syncwarp();
-        if (nb > 0) make_tables(ctl, tabs, R, N, lane);
+        if (nb > 0) make_tables(ctl, tabs, R, N, lane, ROT);
     }
     __syncthreads();
     if (store)
@@ -501,7 +528,7 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
                     if (one_pass) __syncthreads();  // pairs with the final pass's mid-phase barrier
                 }
                 if (p == (one_pass ? 0u : 1u) && b + 1 < nrun)
-                    make_tables(ctl, tabs + ((b + 1) & 1) * r_max, R, N, lane);
+                    make_tables(ctl, tabs + ((b + 1) & 1) * r_max, R, N, lane, ROT);
                 if (late && p + 1 == R) {  // between the final pass's pool stores and its output
                     __syncthreads();
                     form_scale(b, wr + 4u * (N - 1u));
@@ -509,7 +536,7 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
                 }
             } else if (p + 1 < R) {
                 float2 part;
-                pass_quads<QT, false, FULL, EMIT_NONE, 0, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part, 0,
+                pass_quads<QT, false, FULL, EMIT_NONE, 0, OutT, ROT>(rd, wr, tp, q0, lane, m4, half, nq, part, 0,
                                                                nullptr, nullptr, 0, acc);
             } else {
                 float2 part = make_float2(0.f, 0.f);
@@ -517,32 +544,32 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
                 const bool emit = (dec == 1) || (dc + 1 == dec);  // decimation: a block to return
                 const bool whole = ((dec == 1 ? b : e) + 1 < nb) || tail == 0;
                 if (GBM && emit) {
-                    pass_quads<QT, true, FULL, EMIT_GBM, 0, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part,
+                    pass_quads<QT, true, FULL, EMIT_GBM, 0, OutT, ROT>(rd, wr, tp, q0, lane, m4, half, nq, part,
                                                                  nsync, ob, scp, 0, acc);
                 } else if (!store || !emit) {
-                    pass_quads<QT, true, FULL, EMIT_NONE, 0, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part,
+                    pass_quads<QT, true, FULL, EMIT_NONE, 0, OutT, ROT>(rd, wr, tp, q0, lane, m4, half, nq, part,
                                                                   0, ob, scp, 0, acc);
                     if (nsync > 0) __syncthreads();
                     if (nsync > 1) __syncthreads();
                 } else if (!whole) {
-                    pass_quads<QT, true, FULL, EMIT_PART, 0, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part,
+                    pass_quads<QT, true, FULL, EMIT_PART, 0, OutT, ROT>(rd, wr, tp, q0, lane, m4, half, nq, part,
                                                                   nsync, ob, scp, (uint32_t)tail, acc);
                 } else {
                     switch (a) {
                     case 0:
-                        pass_quads<QT, true, FULL, EMIT_WHOLE, 0, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part,
+                        pass_quads<QT, true, FULL, EMIT_WHOLE, 0, OutT, ROT>(rd, wr, tp, q0, lane, m4, half, nq, part,
                                                                        nsync, ob, scp, 0, acc);
                         break;
                     case 1:
-                        pass_quads<QT, true, FULL, EMIT_WHOLE, 1, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part,
+                        pass_quads<QT, true, FULL, EMIT_WHOLE, 1, OutT, ROT>(rd, wr, tp, q0, lane, m4, half, nq, part,
                                                                        nsync, ob, scp, 0, acc);
                         break;
                     case 2:
-                        pass_quads<QT, true, FULL, EMIT_WHOLE, 2, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part,
+                        pass_quads<QT, true, FULL, EMIT_WHOLE, 2, OutT, ROT>(rd, wr, tp, q0, lane, m4, half, nq, part,
                                                                        nsync, ob, scp, 0, acc);
                         break;
                     default:
-                        pass_quads<QT, true, FULL, EMIT_WHOLE, 3, OutT>(rd, wr, tp, q0, lane, m4, half, nq, part,
+                        pass_quads<QT, true, FULL, EMIT_WHOLE, 3, OutT, ROT>(rd, wr, tp, q0, lane, m4, half, nq, part,
                                                                        nsync, ob, scp, 0, acc);
                         break;
                     }
@@ -615,8 +642,12 @@ __global__ void __launch_bounds__(MAXT, MINB) generate_kernel(GenArgs a)
     const uint64_t off = (uint64_t)blockIdx.x * a.out_stride;
     OutT *out = a.out ? reinterpret_cast<OutT *>(a.out) + off : nullptr;
     const GbmArgs none{};
-    run_stream<QT, FULL, OutT, false, VAR>(h, a.pools + h->pool_off, out, off, count, a.warmup_blocks == 0, a.n_max,
-                                      a.r_max, none);
+    if (VAR && var_rotation(h->variant))
+        run_stream<QT, FULL, OutT, false, VAR, true>(h, a.pools + h->pool_off, out, off, count, a.warmup_blocks == 0,
+                                                     a.n_max, a.r_max, none);
+    else
+        run_stream<QT, FULL, OutT, false, VAR, false>(h, a.pools + h->pool_off, out, off, count, a.warmup_blocks == 0,
+                                                      a.n_max, a.r_max, none);
 }
 
 // The fused GBM consumer: every stream of the launch returns steps * ppg
@@ -626,8 +657,12 @@ template <int QT, int MAXT, int MINB, bool FULL>
 __global__ void __launch_bounds__(MAXT, MINB) gbm_kernel(GenArgs a, GbmArgs g)
 {
     StreamHdr *h = a.hdr + blockIdx.x;
-    run_stream<QT, FULL, float, true, true>(h, a.pools + h->pool_off, nullptr, 0, a.count, false, a.n_max, a.r_max,
-                                            g);
+    if (var_rotation(h->variant))
+        run_stream<QT, FULL, float, true, true, true>(h, a.pools + h->pool_off, nullptr, 0, a.count, false, a.n_max,
+                                                      a.r_max, g);
+    else
+        run_stream<QT, FULL, float, true, true, false>(h, a.pools + h->pool_off, nullptr, 0, a.count, false, a.n_max,
+                                                       a.r_max, g);
 }
 
 // Work of a batch: per stream an output offset (elements from `out`) and a
@@ -658,8 +693,13 @@ __global__ void __launch_bounds__(MAXT, MINB) persist_kernel(GenArgs a, BatchArg
         const uint32_t si = bq.order[it];
         StreamHdr *h = a.hdr + si;
         const uint64_t off = bq.offsets[si];
-        run_stream<QT, FULL, OutT, false, VAR>(h, a.pools + h->pool_off, reinterpret_cast<OutT *>(a.out) + off, off,
-                                          bq.counts[si], true, a.n_max, a.r_max, none);
+        OutT *o = reinterpret_cast<OutT *>(a.out) + off;
+        if (VAR && var_rotation(h->variant))
+            run_stream<QT, FULL, OutT, false, VAR, true>(h, a.pools + h->pool_off, o, off, bq.counts[si], true, a.n_max,
+                                                         a.r_max, none);
+        else
+            run_stream<QT, FULL, OutT, false, VAR, false>(h, a.pools + h->pool_off, o, off, bq.counts[si], true,
+                                                          a.n_max, a.r_max, none);
     }
 }
 

@@ -2,7 +2,8 @@
 
 Section 5.5: the chi-squared approximations (a) rann4's, (b) Wilson-Hilferty,
 no correction; fastnorm's reserved value taken from the current pool.
-Section 5.7: pool decimation (the values of every d-th block).  Integers
+Section 5.7: pool decimation (the values of every d-th block).  Section
+5.3: rann4's plane rotations in place of the 4x4 update.  Integers
 (generator words, block counts) bit-exact; FP32 values within the error
 model of tests/_parity.py, where a decimated stream's returned block b has
 seen R (W + d (b + 1)) passes.
@@ -31,16 +32,17 @@ def _passes(count, N, R, d=1, first=0):
     return R * (W + d * (b + 1))
 
 
-def _check(wn, N, R, chi2="c", reserve="previous", d=1, seeds=(3, 4), chunks=(None,)):
-    h = wn.wn_create_ex([N] * len(seeds), [R] * len(seeds), list(seeds), chi2=chi2, reserve=reserve, decimate=d)
-    refs = [oracle.Stream(N, R, s, chi2=chi2, reserve=reserve, decimate=d) for s in seeds]
+def _check(wn, N, R, chi2="c", reserve="previous", d=1, seeds=(3, 4), chunks=(None,), update="quad"):
+    h = wn.wn_create_ex([N] * len(seeds), [R] * len(seeds), list(seeds), chi2=chi2, reserve=reserve, decimate=d,
+                        update=update)
+    refs = [oracle.Stream(N, R, s, chi2=chi2, reserve=reserve, decimate=d, update=update) for s in seeds]
     done = 0
     for c in chunks:
         c = c if c is not None else 4 * (N - 1) + 5
         got = _gen(wn, h, c)
         for i, ref in enumerate(refs):
             assert_fp32_close(got[i], ref.generate(c), _passes(c, N, R, d, first=done // (N - 1)),
-                              f"N={N} R={R} chi2={chi2} reserve={reserve} d={d}")
+                              f"N={N} R={R} chi2={chi2} reserve={reserve} d={d} update={update}")
         done += c
     for i, ref in enumerate(refs):
         st = wn.wn_get_state(h, i)
@@ -63,6 +65,31 @@ def test_reserve_from_current_pool(wn, N, R):
 def test_pool_decimation(wn, N, R, d):
     # calls cut blocks anywhere: the leftover of a returned block carries over
     _check(wn, N, R, d=d, chunks=(1, N - 2, 3 * (N - 1) + 7, N))
+
+
+@pytest.mark.parametrize("N,R", [(1024, 4), (64, 3), (4096, 2), (16384, 1), (16, 5)])
+def test_rotation_form(wn, N, R):
+    _check(wn, N, R, update="rotation", chunks=(N - 2, 3 * (N - 1) + 7))
+
+
+def test_rotation_with_other_variants(wn):
+    _check(wn, 256, 2, update="rotation", chi2="a", d=3)
+    _check(wn, 1024, 1, update="rotation", reserve="current", chi2="b")
+
+
+def test_rotation_batch_equals_per_stream(wn):
+    import torch
+    Ns, Rs = [1024, 4096, 64], [4, 2, 3]
+    counts = np.array([5000, 70_000, 333], dtype=np.uint64)
+    offs = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.uint64)
+    ha = wn.wn_create_ex(Ns, Rs, [7, 8, 9], update="rotation")
+    out = torch.empty(int(counts.sum()), device="cuda")
+    wn.wn_generate_batch(out, counts, offs, ha, wn.WN_F32, True)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for i in range(3):
+        hb = wn.wn_create_ex([Ns[i]], [Rs[i]], [7 + i], update="rotation")
+        assert np.array_equal(got[int(offs[i]):int(offs[i] + counts[i])], _gen(wn, hb, int(counts[i]))[0])
 
 
 def test_variants_combined_and_16bit(wn):
@@ -106,3 +133,5 @@ def test_options_out_of_range_rejected(wn):
         wn.wn_create_ex([64], [2], [1], decimate=256)
     with pytest.raises(ValueError):
         wn.wn_create_ex([64], [2], [1], chi2="d")
+    with pytest.raises(ValueError):
+        wn.wn_create_ex([64], [2], [1], update="hex")
