@@ -120,6 +120,7 @@ struct wn_stream {
     uint32_t smem_base = 0;
     bool uniform_N = true;  // every stream has pool n_max
     int sms = 0;  // multiprocessors of the device
+    int smem_optin = 0;  // largest dynamic shared memory a CTA may request
     // batches (wn_generate_batch): per-stream descriptors on the device, one
     // claim counter per pool-size group, branch streams for the groups, the
     // tuned shape per pool size, and the last captured graph
@@ -254,17 +255,68 @@ void advance_k_one(wn_stream *s, uint32_t i, uint64_t count)
 // One pool-size group of a batch: its streams occupy order[start, start+len).
 struct Group {
     uint32_t N = 0, r_max = 0, start = 0, len = 0;
+    bool exclusive = false;  // long serial chains: one CTA per SM, lowest-latency shape
 };
 
+// The lowest-latency shape for a lone stream (8 quadruples per thread,
+// measured on single streams of pools 1024..16384); small pools keep the
+// default.
+LaunchCfg latency_cfg(uint32_t N)
+{
+    const uint32_t nq = N / 4;
+    if (nq < 256) return pick_cfg(N);
+    const LaunchCfg c{8, nq / 8 + 32 <= 160 ? 160 : 544, nq / 8};
+    return cfg_ok(c, N) ? c : pick_cfg(N);
+}
+
 // Groups streams by pool size and orders each group longest first (cost
-// counts[i] (R_i + 1): a block costs R passes plus its stores).
+// counts[i] (R_i + 1): a block costs R passes plus its stores).  A stream is
+// a serial chain of blocks, so a request whose chain alone outlasts the
+// whole batch's throughput time -- estimated passes x a per-pass latency of
+// about 400 + N/20 ns against 0.34 ps per value-pass over the machine --
+// would set the batch's length; up to a third of the SMs' worth of such
+// requests (longest first) get exclusive groups instead: one CTA per SM with
+// the lowest-latency shape, so that no other CTA shares their SM.
 std::vector<Group> plan_batch(const wn_stream *s, const uint64_t *counts, std::vector<uint32_t> &order)
 {
-    std::map<uint32_t, std::vector<uint32_t>> by_n;
-    for (uint32_t i = 0; i < s->n; ++i) by_n[s->N[i]].push_back(i);
+    std::vector<double> chain(s->n);
+    double thr = 0.0;
+    for (uint32_t i = 0; i < s->n; ++i) {
+        const double N = s->N[i];
+        chain[i] = std::ceil((double)counts[i] / (N - 1.0)) * s->R[i] * (400.0 + N / 20.0) * 1e-9;
+        thr += (double)counts[i] * (s->R[i] + 0.5) * (N >= 16384 ? 1.3 : 1.0) * 0.34e-12;
+    }
+    std::vector<uint32_t> by_chain(s->n);
+    for (uint32_t i = 0; i < s->n; ++i) by_chain[i] = i;
+    std::sort(by_chain.begin(), by_chain.end(),
+              [&](uint32_t x, uint32_t y) { return chain[x] != chain[y] ? chain[x] > chain[y] : x < y; });
+    std::vector<char> crit(s->n, 0);
+    std::map<uint32_t, std::vector<uint32_t>> by_n, crit_n;
+    for (uint32_t i = 0; i < s->n; ++i) by_n[s->N[i]];
+    const uint32_t max_crit = (uint32_t)std::max(1, s->sms / 3);
+    for (uint32_t k = 0; k < s->n && k < max_crit; ++k) {
+        const uint32_t i = by_chain[k];
+        if (!(chain[i] > thr) || counts[i] == 0) break;
+        if (by_n.size() + crit_n.size() + (crit_n.count(s->N[i]) ? 0 : 1) > 16) break;  // one claim counter each
+        crit[i] = 1;
+        crit_n[s->N[i]].push_back(i);
+    }
+    for (uint32_t i = 0; i < s->n; ++i)
+        if (!crit[i]) by_n[s->N[i]].push_back(i);
     std::vector<Group> groups;
     order.clear();
+    for (auto &kv : crit_n) {
+        Group g;
+        g.N = kv.first;
+        g.exclusive = true;
+        g.start = (uint32_t)order.size();
+        g.len = (uint32_t)kv.second.size();
+        for (uint32_t i : kv.second) g.r_max = std::max(g.r_max, s->R[i]);
+        order.insert(order.end(), kv.second.begin(), kv.second.end());
+        groups.push_back(g);
+    }
     for (auto &kv : by_n) {
+        if (kv.second.empty()) continue;
         auto &v = kv.second;
         std::stable_sort(v.begin(), v.end(), [&](uint32_t x, uint32_t y) {
             return counts[x] * (s->R[x] + 1ull) > counts[y] * (s->R[y] + 1ull);
@@ -333,9 +385,10 @@ wn_status enqueue_batch(wn_stream *s, const std::vector<Group> &groups, void *ou
         bq.counts = s->d_bcounts;
         bq.n_items = g.len;
         bq.queue = s->d_queue + gi;
-        const LaunchCfg c = group_cfg(s, g.N);
+        const LaunchCfg c = g.exclusive ? latency_cfg(g.N) : group_cfg(s, g.N);
         const bool full = (uint64_t)c.threads * c.qt == g.N / 4;
-        const size_t smem = wn::gen_smem_bytes(s->smem_base, g.N, g.r_max);
+        size_t smem = wn::gen_smem_bytes(s->smem_base, g.N, g.r_max);
+        if (g.exclusive) smem = std::max(smem, (size_t)s->smem_optin);  // nothing else fits on its SM
         cudaError_t e;
         switch (dt) {
         case WN_F32: e = wn::launch_persist_f32(a, bq, c, full, s->var, smem, s->sms, b); break;
@@ -436,6 +489,8 @@ wn_stream *alloc_handle(uint32_t n_streams, const uint32_t *pool_N, const uint32
     }
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&s->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_hdr, sizeof(wn::StreamHdr) * n_streams);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_pools, sizeof(float) * off);
     if (e != cudaSuccess) {
@@ -977,6 +1032,7 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
     std::map<uint32_t, LaunchCfg> chosen;
     for (size_t gi = 0; gi < groups.size() && e == cudaSuccess; ++gi) {
         const Group &g = groups[gi];
+        if (g.exclusive) continue;  // fixed lowest-latency shape
         const uint32_t nq = g.N / 4;
         float best_ms = 1e30f;
         LaunchCfg best = pick_cfg(g.N);
