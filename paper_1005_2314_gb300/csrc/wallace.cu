@@ -197,6 +197,44 @@ LaunchCfg pick_cfg(uint32_t n_max)
     return {8, 544, nq / 8};
 }
 
+// The latency mode (two control warps beside the compute warps; see
+// run_stream_lat) serves launches of few streams of the plain method, where
+// each stream's serial chain of blocks sets the time.  Its shape: the user's
+// (or the tuner's) when two control warps fit in its thread bound, else four
+// compute warps (measured best for lone streams of pools 1024 and 4096: 2 x
+// 128 and 8 x 128), fewer for small pools.  false: no such shape (pools above
+// 8192 keep the ordinary kernel).
+bool fits_latency(const LaunchCfg &c, uint32_t n_max)
+{
+    return cfg_ok(c, n_max) && c.threads + 64 <= (uint32_t)c.maxt;
+}
+
+bool latency_default(uint32_t n_max, LaunchCfg &out)
+{
+    const uint32_t nq = n_max / 4;
+    const uint32_t t = nq >= 128 ? 128u : std::max(32u, (nq + 31u) / 32u * 32u);
+    const int qt = (int)std::max(1u, nq / t);
+    for (const auto &k : wn::kShapes) {
+        const LaunchCfg c{k[0], k[1], t};
+        if (k[0] == qt && fits_latency(c, n_max)) {
+            out = c;
+            return true;
+        }
+    }
+    return false;
+}
+
+bool latency_cfg_for(const wn_stream *s, LaunchCfg &out)
+{
+    if (s->var || (uint32_t)s->n > (uint32_t)std::max(1, s->sms / 2)) return false;
+    if (s->has_cfg) {
+        if (!fits_latency(s->cfg, s->n_max)) return false;
+        out = s->cfg;
+        return true;
+    }
+    return latency_default(s->n_max, out);
+}
+
 wn_status launch_generate(wn_stream *s, void *out, uint64_t count, uint32_t warmup, wn_dtype dt,
                           cudaStream_t cs)
 {
@@ -210,11 +248,23 @@ wn_status launch_generate(wn_stream *s, void *out, uint64_t count, uint32_t warm
     a.n_max = s->n_max;
     a.r_max = s->r_max;
     a.warmup_blocks = warmup;
-    const LaunchCfg c = s->has_cfg ? s->cfg : pick_cfg(s->n_max);
     const size_t smem = wn::gen_smem_bytes(s->smem_base, s->n_max, s->r_max);
+    cudaError_t e;
+    LaunchCfg lc;
+    if (warmup == 0 && count > 0 && latency_cfg_for(s, lc)) {
+        const bool full = s->uniform_N && (uint64_t)lc.threads * lc.qt == s->n_max / 4;
+        switch (dt) {
+        case WN_F32: e = wn::launch_latency_f32(a, lc, full, smem, cs); break;
+        case WN_BF16: e = wn::launch_latency_bf16(a, lc, full, smem, cs); break;
+        case WN_F16: e = wn::launch_latency_f16(a, lc, full, smem, cs); break;
+        default: return fail(WN_EINVAL, "unknown dtype");
+        }
+        if (e != cudaSuccess) return cuda_fail("generate launch (latency mode)", e);
+        return WN_OK;
+    }
+    const LaunchCfg c = s->has_cfg ? s->cfg : pick_cfg(s->n_max);
     // every stream's quadruples exactly fill the CTA: no per-quadruple checks
     const bool full = s->uniform_N && (uint64_t)c.threads * c.qt == s->n_max / 4;
-    cudaError_t e;
     switch (dt) {
     case WN_F32: e = wn::launch_generate_f32(a, c, full, s->var, smem, cs); break;
     case WN_BF16: e = wn::launch_generate_bf16(a, c, full, s->var, smem, cs); break;

@@ -140,6 +140,25 @@ __device__ __forceinline__ void sts4(uint32_t a, float2 lo, float2 hi)
     asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(lo.x), "f"(lo.y), "f"(hi.x), "f"(hi.y));
 }
 
+__device__ __forceinline__ void sts1(uint32_t a, float v) { asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v)); }
+
+// Named barriers of the latency mode (0 is __syncthreads): the compute warps
+// end each pass on kBarPass among themselves; once per block the two control
+// warps hand over the block's scale and the next block's tables (kBarReady:
+// they arrive, the compute warps wait) and take back the block's partial sums
+// and reserved slot (kBarDone: the compute warps arrive, they wait).  An
+// arrive never waits; the writes before it are fenced for the waiting side.
+constexpr uint32_t kBarPass = 1, kBarReady = 2, kBarDone = 3;
+__device__ __forceinline__ void bar_wait(uint32_t id, uint32_t n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_signal(uint32_t id, uint32_t n)
+{
+    __threadfence_block();
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
 __device__ __forceinline__ unsigned long long f2u(float2 v) { return *reinterpret_cast<unsigned long long *>(&v); }
 __device__ __forceinline__ float2 u2f(unsigned long long v) { return *reinterpret_cast<float2 *>(&v); }
 // Blackwell packed FP32 pairs: one instruction, two IEEE round-to-nearest results.
@@ -278,11 +297,15 @@ struct GbmArgs {
 // scaled output, so that the control warp's scale for this block is visible:
 // one with one pass per block, two when the scale depends on this block's own
 // reserved slot (fastnorm's reserved value).
-template <int QT, bool FINAL, bool FULL, int EMIT, int A, typename OutT, bool ROT>
+//
+// HAND (latency mode): instead of the nsync barriers, the owner of slot N-1
+// stores its value at window address rsv and the compute warps take the
+// scale from the control warps at kBarReady (nthr threads: the whole CTA).
+template <int QT, bool FINAL, bool FULL, int EMIT, int A, typename OutT, bool ROT, bool HAND = false>
 __device__ __forceinline__ void pass_quads(uint32_t rd, uint32_t wr, uint32_t tab, uint32_t q0, uint32_t lane,
                                            uint32_t m4, uint32_t half, uint32_t nq, float2 &part, int nsync,
                                            OutT *__restrict__ ob, const float *sc_ptr, uint32_t n,
-                                           float2 (&acc)[QT][2])
+                                           float2 (&acc)[QT][2], uint32_t rsv = 0, uint32_t nthr = 0)
 {
     const uint4 P = lds4u(tab);
     const float4 sg = lds4(tab + 16u + 16u * (lane & 15u));
@@ -323,11 +346,13 @@ __device__ __forceinline__ void pass_quads(uint32_t rd, uint32_t wr, uint32_t ta
         if (FULL || q < nq) {
             sts4(wr + 16u * q, y[j][0], y[j][1]);
             if (FINAL) part = ffma2(y[j][0], y[j][0], ffma2(y[j][1], y[j][1], part));
+            if (FINAL && HAND && (!FULL || j == QT - 1) && q + 1u == nq) sts1(rsv, y[j][1].y);  // slot N-1
         }
     }
+    if (FINAL && HAND) bar_wait(kBarReady, nthr);
     if (!FINAL || EMIT == EMIT_NONE) return;
-    if (nsync > 0) __syncthreads();
-    if (nsync > 1) __syncthreads();
+    if (!HAND && nsync > 0) __syncthreads();
+    if (!HAND && nsync > 1) __syncthreads();
     const float sc = *sc_ptr;
     const float2 sc2 = make_float2(sc, sc);
     if (EMIT == EMIT_GBM) {
@@ -631,6 +656,193 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
     }
 }
 
+// ---------------------------------------------------------------------------
+// Latency mode (the plain method, launches of few streams: a stream is a
+// serial chain, so a lone stream waits on every step of every block).  Two
+// control warps run beside the compute warps instead of inside their pass
+// barriers: warp 0 forms each block's scale (the FP64 sum of the partial
+// sums, Section 5.5), warp 1 draws and tabulates the next block's passes
+// (Section 5.4); compute warps 2.. own quadruples q0 + 32 j,
+// q0 = (w - 2) 32 QT + l, end each pass on a barrier among themselves, and
+// once per block take the scale and the next tables (kBarReady, in the final
+// pass between its arithmetic and its output) and return the block's partial
+// sums of squares and reserved slot (kBarDone).  The arithmetic is
+// run_stream's (passes, per-warp partial sums, FP64 cross-warp sum, scale,
+// emission): bit-identical for the same compute-warp layout.
+// ---------------------------------------------------------------------------
+template <int QT, bool FULL, typename OutT>
+__device__ __forceinline__ void run_stream_lat(StreamHdr *__restrict__ h, float *__restrict__ pool_g,
+                                               OutT *__restrict__ out, uint64_t out_off, uint64_t count,
+                                               uint32_t n_max, uint32_t r_max)
+{
+    unsigned char *smem = wn_smem;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t N = h->N, nq = N >> 2;
+    const uint32_t base = smem_base();
+    uint32_t dyn;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    const uint32_t W0 = pool_window(base, n_max, r_max);
+    if (W0 + 8u * n_max > base + dyn) {  // layout does not fit: flag and do nothing
+        if (tid == 0) h->flags |= 1u;
+        return;
+    }
+    float *red = reinterpret_cast<float *>(smem);  // [2][32] partial sums by block parity; [par][31]: slot N-1
+    CtlState *ctl = reinterpret_cast<CtlState *>(smem + 256);
+    PassTab *tabs = reinterpret_cast<PassTab *>(smem + 256 + sizeof(CtlState));  // [2][r_max]
+    const uint32_t tabs_s = base + 256u + (uint32_t)sizeof(CtlState);
+    const uint32_t bsz = 4u * n_max;
+    const uint32_t nthr = blockDim.x, ncomp = nthr - 64u, nwc = ncomp >> 5;
+    const uint32_t q0 = (warp - 2u) * 32u * QT + lane;
+    const uint32_t m4 = 4u * N - 1u, half = 2u * N;
+
+    {
+        const float4 *pg4 = reinterpret_cast<const float4 *>(pool_g);
+        float4 *b04 = reinterpret_cast<float4 *>(smem + (W0 - base));
+        for (uint32_t i = tid; i < nq; i += blockDim.x) b04[i] = pg4[i];
+    }
+    const uint32_t k0 = h->k;
+    const float sc_prev = h->scale;
+    const uint64_t left = (uint64_t)(N - 1 - k0);
+    const uint64_t n0 = left < count ? left : count;
+    const uint64_t nb = (count - n0 + (N - 2)) / (N - 1);
+    const uint64_t tail = (count - n0) % (N - 1);
+    const uint32_t R = h->R;
+    if (warp == 0 && lane == 0) {
+        ctl->gx = h->x;
+        ctl->gw = h->w;
+        ctl->sumsq = h->sumsq;
+        ctl->r = (float)h->r;
+        ctl->A = (float)h->A;
+        ctl->B = (float)h->B;
+        ctl->sc[1] = sc_prev;
+    }
+    __syncthreads();
+    if (warp == 1 && nb > 0) make_tables(ctl, tabs, R, N, lane, false);
+    for (uint64_t i = tid; i < n0; i += blockDim.x)
+        out[i] = to_out<OutT>(sc_prev * lds(W0 + 4u * (uint32_t)(k0 + i)));
+    __syncthreads();  // block 0's tables are there and buffer 0 has been read
+
+    uint32_t cb = (uint32_t)((nb * R) & 1u);  // the control warps only need the final buffer
+    if (warp == 0) {
+        for (uint64_t b = 0; b < nb; ++b) {
+            if (b > 0) bar_wait(kBarDone, nthr);
+            double ss;
+            if (b == 0) {
+                ss = ctl->sumsq;
+            } else {
+                const float *rb = red + ((b - 1) & 1) * 32;
+                double v = (lane < nwc) ? (double)rb[lane] : 0.0;
+                for (uint32_t o = 1; o < 32; o <<= 1)
+                    if (o < nwc) v += __shfl_xor_sync(0xffffffffu, v, o);
+                ss = v;
+            }
+            const float r = (b == 0) ? ctl->r : ctl->sc[(b - 1) & 1] * red[((b - 1) & 1) * 32 + 31];
+            const float invNf = 1.0f / (float)N;
+            const float delta = (float)fma(ss, (double)invNf, -1.0);
+            const float c = __frsqrt_rn(1.0f + delta);
+            const float u = fmaf(ctl->A, fmaf(r, r, -1.0f), ctl->B * r) * invNf;
+            const float sv = __fsqrt_rn(1.0f + u) * c;
+            __syncwarp();
+            if (lane == 0) ctl->sc[b & 1] = sv;
+            bar_signal(kBarReady, nthr);
+        }
+    } else if (warp == 1) {
+        for (uint64_t b = 0; b < nb; ++b) {
+            if (b > 0) bar_wait(kBarDone, nthr);
+            if (b + 1 < nb) make_tables(ctl, tabs + ((b + 1) & 1) * r_max, R, N, lane, false);
+            bar_signal(kBarReady, nthr);
+        }
+    } else {
+        float2 acc[QT][2];
+        cb = 0;
+        OutT *ob = out + n0;
+        uint32_t a = (uint32_t)((out_off + n0) & 3u);
+        for (uint64_t b = 0; b < nb; ++b) {
+            const uint32_t tb = tabs_s + (uint32_t)(b & 1) * r_max * (uint32_t)sizeof(PassTab);
+            for (uint32_t p = 0; p < R; ++p) {
+                const uint32_t rd = W0 + cb * bsz, wr = W0 + (cb ^ 1u) * bsz;
+                const uint32_t tp = tb + p * (uint32_t)sizeof(PassTab);
+                if (p + 1 < R) {
+                    float2 part;
+                    pass_quads<QT, false, FULL, EMIT_NONE, 0, OutT, false>(rd, wr, tp, q0, lane, m4, half, nq, part,
+                                                                          0, nullptr, nullptr, 0, acc);
+                } else {
+                    float2 part = make_float2(0.f, 0.f);
+                    const float *scp = &ctl->sc[b & 1];
+                    const uint32_t rsv = base + 4u * ((uint32_t)(b & 1) * 32u + 31u);
+                    const bool whole = (b + 1 < nb) || tail == 0;
+                    if (!whole) {
+                        pass_quads<QT, true, FULL, EMIT_PART, 0, OutT, false, true>(
+                            rd, wr, tp, q0, lane, m4, half, nq, part, 0, ob, scp, (uint32_t)tail, acc, rsv, nthr);
+                    } else {
+                        switch (a) {
+                        case 0:
+                            pass_quads<QT, true, FULL, EMIT_WHOLE, 0, OutT, false, true>(
+                                rd, wr, tp, q0, lane, m4, half, nq, part, 0, ob, scp, 0, acc, rsv, nthr);
+                            break;
+                        case 1:
+                            pass_quads<QT, true, FULL, EMIT_WHOLE, 1, OutT, false, true>(
+                                rd, wr, tp, q0, lane, m4, half, nq, part, 0, ob, scp, 0, acc, rsv, nthr);
+                            break;
+                        case 2:
+                            pass_quads<QT, true, FULL, EMIT_WHOLE, 2, OutT, false, true>(
+                                rd, wr, tp, q0, lane, m4, half, nq, part, 0, ob, scp, 0, acc, rsv, nthr);
+                            break;
+                        default:
+                            pass_quads<QT, true, FULL, EMIT_WHOLE, 3, OutT, false, true>(
+                                rd, wr, tp, q0, lane, m4, half, nq, part, 0, ob, scp, 0, acc, rsv, nthr);
+                            break;
+                        }
+                    }
+                    float ps = part.x + part.y;
+                    for (int o = 16; o > 0; o >>= 1) ps += __shfl_xor_sync(0xffffffffu, ps, o);
+                    if (lane == 0) red[(b & 1) * 32 + (warp - 2)] = ps;
+                    if (b + 1 < nb) bar_signal(kBarDone, nthr);
+                }
+                cb ^= 1u;
+                bar_wait(kBarPass, ncomp);
+            }
+            ob += N - 1;
+            a = (a + N - 1) & 3u;
+        }
+    }
+    __syncthreads();
+
+    {
+        float4 *pw4 = reinterpret_cast<float4 *>(pool_g);
+        for (uint32_t i = tid; i < nq; i += blockDim.x) pw4[i] = lds4(W0 + cb * bsz + 16u * i);
+    }
+    if (warp == 0 && nb > 0) {
+        const float *rb = red + ((nb - 1) & 1) * 32;
+        double v = (lane < nwc) ? (double)rb[lane] : 0.0;
+        for (uint32_t o = 1; o < 32; o <<= 1)
+            if (o < nwc) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) {
+            const float sc = ctl->sc[(nb - 1) & 1];
+            h->x = ctl->gx;
+            h->w = ctl->gw;
+            h->sumsq = v;
+            h->r = (double)(sc * red[((nb - 1) & 1) * 32 + 31]);
+            h->scale = sc;
+            h->k = tail == 0 ? N - 1 : (uint32_t)tail;
+            h->blocks += nb;
+        }
+    } else if (tid == 0 && nb == 0) {
+        h->k = k0 + (uint32_t)n0;
+    }
+}
+
+// Latency-mode generate kernel: one CTA per stream, blockDim = compute
+// threads + 64 (two control warps).
+template <int QT, int MAXT, int MINB, bool FULL, typename OutT>
+__global__ void __launch_bounds__(MAXT, MINB) latency_kernel(GenArgs a)
+{
+    StreamHdr *h = a.hdr + blockIdx.x;
+    const uint64_t off = (uint64_t)blockIdx.x * a.out_stride;
+    run_stream_lat<QT, FULL, OutT>(h, a.pools + h->pool_off, reinterpret_cast<OutT *>(a.out) + off, off, a.count,
+                                   a.n_max, a.r_max);
+}
+
 // FULL: every stream of the launch has exactly (blockDim.x - 32) * QT
 // quadruples, so no quadruple index needs a bounds check.
 template <int QT, int MAXT, int MINB, bool FULL, typename OutT, bool VAR>
@@ -785,6 +997,39 @@ cudaError_t launch_generate_t(const GenArgs &a, const LaunchCfg &c, bool full, b
     default: return cudaErrorInvalidValue;
     }
 }
+
+template <int QT, int MAXT, int MINB, typename OutT>
+cudaError_t launch_latency_shape(const GenArgs &a, uint32_t threads, bool full, size_t smem, cudaStream_t cs)
+{
+    auto kern = full ? latency_kernel<QT, MAXT, MINB, true, OutT> : latency_kernel<QT, MAXT, MINB, false, OutT>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<a.n_streams, threads + 64, smem, cs>>>(a);  // + the two control warps
+    return cudaGetLastError();
+}
+
+// Latency-mode launch for one output type: the shape's thread bound must
+// admit the compute threads plus two control warps.
+template <typename OutT>
+cudaError_t launch_latency_t(const GenArgs &a, const LaunchCfg &c, bool full, size_t smem, cudaStream_t cs)
+{
+    if (c.threads + 64 > (uint32_t)c.maxt) return cudaErrorInvalidValue;
+    switch (c.qt * 10000 + c.maxt) {
+    case 1 * 10000 + 1024: return launch_latency_shape<1, 1024, 1, OutT>(a, c.threads, full, smem, cs);
+    case 2 * 10000 + 544: return launch_latency_shape<2, 544, 2, OutT>(a, c.threads, full, smem, cs);
+    case 4 * 10000 + 288: return launch_latency_shape<4, 288, 4, OutT>(a, c.threads, full, smem, cs);
+    case 8 * 10000 + 160: return launch_latency_shape<8, 160, 4, OutT>(a, c.threads, full, smem, cs);
+    case 8 * 10000 + 544: return launch_latency_shape<8, 544, 1, OutT>(a, c.threads, full, smem, cs);
+    case 16 * 10000 + 288: return launch_latency_shape<16, 288, 1, OutT>(a, c.threads, full, smem, cs);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_latency_f32(const GenArgs &a, const LaunchCfg &c, bool full, size_t smem, cudaStream_t cs);
+cudaError_t launch_latency_bf16(const GenArgs &a, const LaunchCfg &c, bool full, size_t smem, cudaStream_t cs);
+cudaError_t launch_latency_f16(const GenArgs &a, const LaunchCfg &c, bool full, size_t smem, cudaStream_t cs);
 
 cudaError_t launch_generate_f32(const GenArgs &a, const LaunchCfg &c, bool full, bool var, size_t smem,
                                cudaStream_t cs);
