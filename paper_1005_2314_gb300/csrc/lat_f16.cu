@@ -1,10 +1,16 @@
-// lat_f16.cu -- the latency-mode generate kernel instantiated for __half output (a
-// translation unit of its own, so it compiles in parallel with the others).
+// lat_f16.cu -- the latency-mode generate and persistent kernels for __half
+// output (a translation unit of its own, so it compiles in parallel).
 #include "wn_gen.cuh"
 
 namespace wn {
 cudaError_t launch_latency_f16(const GenArgs &a, const LaunchCfg &c, bool full, size_t smem, cudaStream_t cs)
 {
     return launch_latency_t<__half>(a, c, full, smem, cs);
+}
+
+cudaError_t launch_persist_lat_f16(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full, size_t smem,
+                                  int sms, cudaStream_t cs)
+{
+    return launch_persist_lat_t<__half>(a, bq, c, full, smem, sms, cs);
 }
 }  // namespace wn

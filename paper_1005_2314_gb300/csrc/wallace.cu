@@ -134,6 +134,11 @@ struct wn_stream {
     void *g_out = nullptr;
     int g_dtype = -1;
     std::vector<uint64_t> g_counts, g_offsets;
+    // batches: latency-mode persistent kernels for exclusive groups (1) or for
+    // every group whose pool size has a latency shape (2); 0: never.  The
+    // batch tuner's choice per pool size (group_lat) overrides it.
+    int batch_lat = 2;
+    std::map<uint32_t, bool> group_lat;
     // some stream runs a method variant (wn_create_ex, wn_load): use the
     // kernels that read StreamHdr::variant (the others compile the plain method)
     bool var = false;
@@ -435,11 +440,27 @@ wn_status enqueue_batch(wn_stream *s, const std::vector<Group> &groups, void *ou
         bq.counts = s->d_bcounts;
         bq.n_items = g.len;
         bq.queue = s->d_queue + gi;
-        const LaunchCfg c = g.exclusive ? latency_cfg(g.N) : group_cfg(s, g.N);
-        const bool full = (uint64_t)c.threads * c.qt == g.N / 4;
         size_t smem = wn::gen_smem_bytes(s->smem_base, g.N, g.r_max);
         if (g.exclusive) smem = std::max(smem, (size_t)s->smem_optin);  // nothing else fits on its SM
         cudaError_t e;
+        LaunchCfg lc;
+        const auto tuned = s->group_lat.find(g.N);
+        const bool want_lat = g.exclusive ? s->batch_lat >= 1
+                                          : (tuned != s->group_lat.end() ? tuned->second : s->batch_lat >= 2);
+        if (!s->var && want_lat && latency_default(g.N, lc)) {
+            const bool lfull = (uint64_t)lc.threads * lc.qt == g.N / 4;
+            switch (dt) {
+            case WN_F32: e = wn::launch_persist_lat_f32(a, bq, lc, lfull, smem, s->sms, b); break;
+            case WN_BF16: e = wn::launch_persist_lat_bf16(a, bq, lc, lfull, smem, s->sms, b); break;
+            default: e = wn::launch_persist_lat_f16(a, bq, lc, lfull, smem, s->sms, b); break;
+            }
+            if (e != cudaSuccess) return cuda_fail("wn_generate_batch: launch", e);
+            WN_CU(cudaEventRecord(s->join[gi], b));
+            WN_CU(cudaStreamWaitEvent(cs, s->join[gi], 0));
+            continue;
+        }
+        const LaunchCfg c = g.exclusive ? latency_cfg(g.N) : group_cfg(s, g.N);
+        const bool full = (uint64_t)c.threads * c.qt == g.N / 4;
         switch (dt) {
         case WN_F32: e = wn::launch_persist_f32(a, bq, c, full, s->var, smem, s->sms, b); break;
         case WN_BF16: e = wn::launch_persist_bf16(a, bq, c, full, s->var, smem, s->sms, b); break;
@@ -1080,6 +1101,7 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
         return r;
     };
     std::map<uint32_t, LaunchCfg> chosen;
+    std::map<uint32_t, bool> chosen_lat;
     for (size_t gi = 0; gi < groups.size() && e == cudaSuccess; ++gi) {
         const Group &g = groups[gi];
         if (g.exclusive) continue;  // fixed lowest-latency shape
@@ -1121,6 +1143,35 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
                 }
             }
         chosen[g.N] = best;
+        // the latency mode with its default shape, if it beats every ordinary shape
+        LaunchCfg lc;
+        bool lat = false;
+        if (e == cudaSuccess && !s->var && latency_default(g.N, lc)) {
+            float times[2] = {0.f, 0.f};
+            const bool lfull = (uint64_t)lc.threads * lc.qt == nq;
+            const size_t smem = wn::gen_smem_bytes(s->smem_base, g.N, g.r_max);
+            for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+                e = restore();
+                if (e == cudaSuccess) e = cudaMemsetAsync(s->d_queue, 0, sizeof(uint32_t) * 16, cs);
+                if (e == cudaSuccess) e = cudaEventRecord(e0, cs);
+                if (e == cudaSuccess) {
+                    wn::GenArgs a{s->d_hdr, s->d_pools, out, 0, 0, g.len, g.N, g.r_max, 0};
+                    wn::BatchArgs bq{s->d_border + g.start, s->d_boffsets, s->d_bcounts, g.len, s->d_queue};
+                    switch (dtype) {
+                    case WN_F32: e = wn::launch_persist_lat_f32(a, bq, lc, lfull, smem, s->sms, cs); break;
+                    case WN_BF16: e = wn::launch_persist_lat_bf16(a, bq, lc, lfull, smem, s->sms, cs); break;
+                    default: e = wn::launch_persist_lat_f16(a, bq, lc, lfull, smem, s->sms, cs); break;
+                    }
+                }
+                if (e == cudaSuccess) e = cudaEventRecord(e1, cs);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) times[rep - 1] = ms;
+            }
+            lat = e == cudaSuccess && std::min(times[0], times[1]) < best_ms;
+        }
+        chosen_lat[g.N] = lat;
     }
     if (e == cudaSuccess) e = restore();
     if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
@@ -1130,6 +1181,7 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
     if (e1) cudaEventDestroy(e1);
     if (e != cudaSuccess) return cuda_fail("wn_autotune_batch", e);
     for (auto &kv : chosen) s->group_cfg[kv.first] = kv.second;
+    for (auto &kv : chosen_lat) s->group_lat[kv.first] = kv.second;
     if (s->gexec) {  // a captured graph used the old shapes
         cudaGraphExecDestroy(s->gexec);
         s->gexec = nullptr;

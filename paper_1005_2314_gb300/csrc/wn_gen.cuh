@@ -1010,6 +1010,68 @@ cudaError_t launch_latency_shape(const GenArgs &a, uint32_t threads, bool full, 
     return cudaGetLastError();
 }
 
+// Persistent latency-mode kernel (batches): claims streams like
+// persist_kernel and runs each with run_stream_lat.
+template <int QT, int MAXT, int MINB, bool FULL, typename OutT>
+__global__ void __launch_bounds__(MAXT, MINB) persist_lat_kernel(GenArgs a, BatchArgs bq)
+{
+    CtlState *ctl = reinterpret_cast<CtlState *>(wn_smem + 256);
+    for (;;) {
+        __syncthreads();  // the previous stream is done with shared memory
+        if (threadIdx.x == 0) ctl->item = atomicAdd(bq.queue, 1u);
+        __syncthreads();
+        const uint32_t it = ctl->item;
+        if (it >= bq.n_items) return;
+        const uint32_t si = bq.order[it];
+        StreamHdr *h = a.hdr + si;
+        const uint64_t off = bq.offsets[si];
+        run_stream_lat<QT, FULL, OutT>(h, a.pools + h->pool_off, reinterpret_cast<OutT *>(a.out) + off, off,
+                                       bq.counts[si], a.n_max, a.r_max);
+    }
+}
+
+template <int QT, int MAXT, int MINB, typename OutT>
+cudaError_t launch_persist_lat_shape(const GenArgs &a, const BatchArgs &bq, uint32_t threads, bool full,
+                                     size_t smem, int sms, cudaStream_t cs)
+{
+    auto kern = full ? persist_lat_kernel<QT, MAXT, MINB, true, OutT> : persist_lat_kernel<QT, MAXT, MINB, false, OutT>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)threads + 64, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const uint32_t grid = std::min<uint32_t>(bq.n_items, (uint32_t)(per_sm * sms));
+    if (grid == 0) return cudaSuccess;
+    kern<<<grid, threads + 64, smem, cs>>>(a, bq);
+    return cudaGetLastError();
+}
+
+template <typename OutT>
+cudaError_t launch_persist_lat_t(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full, size_t smem,
+                                 int sms, cudaStream_t cs)
+{
+    if (c.threads + 64 > (uint32_t)c.maxt) return cudaErrorInvalidValue;
+    switch (c.qt * 10000 + c.maxt) {
+    case 1 * 10000 + 1024: return launch_persist_lat_shape<1, 1024, 1, OutT>(a, bq, c.threads, full, smem, sms, cs);
+    case 2 * 10000 + 544: return launch_persist_lat_shape<2, 544, 2, OutT>(a, bq, c.threads, full, smem, sms, cs);
+    case 4 * 10000 + 288: return launch_persist_lat_shape<4, 288, 4, OutT>(a, bq, c.threads, full, smem, sms, cs);
+    case 8 * 10000 + 160: return launch_persist_lat_shape<8, 160, 4, OutT>(a, bq, c.threads, full, smem, sms, cs);
+    case 8 * 10000 + 544: return launch_persist_lat_shape<8, 544, 1, OutT>(a, bq, c.threads, full, smem, sms, cs);
+    case 16 * 10000 + 288: return launch_persist_lat_shape<16, 288, 1, OutT>(a, bq, c.threads, full, smem, sms, cs);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_persist_lat_f32(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full,
+                                   size_t smem, int sms, cudaStream_t cs);
+cudaError_t launch_persist_lat_bf16(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full,
+                                    size_t smem, int sms, cudaStream_t cs);
+cudaError_t launch_persist_lat_f16(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full,
+                                   size_t smem, int sms, cudaStream_t cs);
+
 // Latency-mode launch for one output type: the shape's thread bound must
 // admit the compute threads plus two control warps.
 template <typename OutT>
