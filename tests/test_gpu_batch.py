@@ -103,3 +103,25 @@ def test_uneven_recipe_scaled_down(wn):
     got = out.cpu().numpy()
     pick = np.arange(0, 300, 37)
     _check(got, N[pick], R[pick], seeds[pick], counts[pick], offsets[pick])
+
+
+def test_latency_mode_is_bit_identical_to_the_ordinary_kernel(wn):
+    # Few streams run in the latency mode (two control warps, named-barrier
+    # handoffs); many streams run the ordinary kernel.  With the same
+    # compute-warp layout the arithmetic is the same, so a stream's values
+    # must agree bit for bit.
+    import torch
+    N, R, shape = 1024, 2, (2, 128)
+    n_many = 200  # more than half the SMs: the ordinary kernel
+    many = wn.wn_create_streams([N] * n_many, [R] * n_many, list(range(1, n_many + 1)))
+    wn.wn_set_config(many, *shape)
+    few = wn.wn_create_streams([N] * 3, [R] * 3, [1, 2, 3])
+    wn.wn_set_config(few, *shape)
+    count = 5 * (N - 1) + 11
+    a = torch.empty(n_many * count, device="cuda")
+    b = torch.empty(3 * count, device="cuda")
+    for _ in range(2):  # the second call continues mid-block
+        wn.wn_generate(a, count, many)
+        wn.wn_generate(b, count, few)
+        torch.cuda.synchronize()
+        assert torch.equal(a.view(n_many, count)[:3], b.view(3, count))
