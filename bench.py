@@ -399,8 +399,8 @@ def run_ours(args, rank, world, local_rank):
         dt = max_over_ranks(time.perf_counter() - t, world, dev)
         e2e = {"value": world * variates * e_steps / dt, "unit": "variates/s", "h2d_bytes_per_step": 0,
                "d2h_bytes_per_step": variates * 4, "steps": e_steps,
-               "how": "wn_generate_host into pinned host memory: generation in 256 MiB chunks with "
-                      "D2H copies overlapped on a second stream; host wall clock"}
+               "how": "wn_generate_host into pinned host memory (the kernel stores straight into it over "
+                      "the host link); host wall clock"}
         del host
     except Exception as ex:  # pinned allocation can fail on small hosts
         e2e = {"value": None, "unit": "variates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,

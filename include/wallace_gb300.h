@@ -143,12 +143,14 @@ wn_status wn_generate_ex(void *out, uint64_t count, wn_stream *s, wn_dtype dtype
 /*
  * wn_generate_host -- as wn_generate_ex, but the values land in HOST memory:
  * stream i's values go to host_out[i*count .. i*count + count) (elements of
- * `dtype`).  The library generates in chunks into a device staging area the
- * handle owns (allocated on first use, two buffers of at most 256 MiB) and
- * copies each chunk to the host on a second CUDA stream while the next chunk
- * is generated.  host_out should be page-locked (cudaHostAlloc or a pinned
- * torch tensor) for full copy speed.  Asynchronous on cuda_stream: the
- * values are in place once cuda_stream has been synchronised.
+ * `dtype`).  If host_out is page-locked memory the device can address
+ * (cudaHostAlloc, cudaHostRegister, a pinned torch tensor) and 16-byte
+ * aligned, the kernel writes it directly over the host link.  Otherwise the
+ * library generates in chunks into a device staging area the handle owns
+ * (allocated on first use, two buffers of at most 256 MiB) and copies each
+ * chunk to the host on a second CUDA stream while the next chunk is
+ * generated.  Asynchronous on cuda_stream: the values are in place once
+ * cuda_stream has been synchronised.
  */
 wn_status wn_generate_host(void *host_out, uint64_t count, wn_stream *s, wn_dtype dtype, void *cuda_stream);
 

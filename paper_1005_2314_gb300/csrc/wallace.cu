@@ -980,6 +980,24 @@ wn_status wn_generate_host(void *host_out, uint64_t count, wn_stream *s, wn_dtyp
     if (dtype != WN_F32 && dtype != WN_BF16 && dtype != WN_F16) return fail(WN_EINVAL, "wn_generate_host: unknown dtype");
     if (count == 0) return WN_OK;
     if (!host_out) return fail(WN_EINVAL, "wn_generate_host: NULL output");
+    cudaStream_t cs0 = reinterpret_cast<cudaStream_t>(cuda_stream);
+    {
+        // page-locked host memory that the device can address (every
+        // cudaHostAlloc'd or registered buffer under unified addressing): the
+        // kernel stores straight into it over the host link, which on GB300
+        // beats staging plus copies for large requests (measured 182 vs 77 GB/s
+        // for 16 GiB: the pitched copies of the staged path run far below the
+        // copy engine's 193 GB/s)
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, host_out) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            pa.devicePointer && reinterpret_cast<uintptr_t>(pa.devicePointer) % 16 == 0) {
+            const wn_status st = launch_generate(s, pa.devicePointer, count, 0, dtype, cs0);
+            if (st != WN_OK) return st;
+            advance_k(s, count);
+            return WN_OK;
+        }
+        cudaGetLastError();  // an unregistered pointer is not an error here
+    }
     const size_t esize = dtype == WN_F32 ? 4 : 2;
     const size_t kStageMax = size_t(256) << 20;
     if (!s->d_stage[0]) {

@@ -1,6 +1,7 @@
-// wn_gen.cuh -- the generate kernel of Wallace's maximum-entropy normal
-// generator for sm_103a (Brent, arXiv:1005.2314, Section 5), as templates
-// instantiated per output type in gen_f32.cu, gen_bf16.cu and gen_f16.cu.
+// wn_gen.cuh -- the kernels of Wallace's maximum-entropy normal generator for
+// sm_103a (Brent, arXiv:1005.2314, Section 5), as templates instantiated per
+// output type and kernel kind in gen_*.cu (generate), persist_*.cu (batches),
+// lat_*.cu (latency mode) and gbm.cu (the fused Monte Carlo consumer).
 //
 // One CTA owns one stream for the whole call and keeps its pool of N values
 // in shared memory.  A pass gathers each quadruple through the affine
@@ -16,7 +17,9 @@
 // wavefronts, not by HBM):
 //  * warp 0 is a control warp: it draws and tabulates the next block's passes
 //    and forms each block's scale (FP64 sum of the compute warps' partial sums
-//    of squares, then FP32) while the compute warps run passes;
+//    of squares, then FP32) while the compute warps run passes (the latency
+//    mode for few streams splits this between two control warps outside the
+//    pass barriers; see run_stream_lat);
 //  * gathers are conflict-free (alpha odd: a warp's 32 consecutive
 //    quadruples hit 32 banks) and their addresses cost one LOP3 each, because
 //    the pool buffers sit at shared-window addresses that are multiples of

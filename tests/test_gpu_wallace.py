@@ -98,16 +98,19 @@ def test_continuation_is_bit_exact_and_matches_oracle(wn, torch):
     assert_fp32_close(whole, ref, passes_fresh(total, N, R))
 
 
+@pytest.mark.parametrize("pinned", [True, False])
 @pytest.mark.parametrize("Ns,Rs,half", [([1024, 4096, 64], [2, 2, 3], 50_001),
                                          ([64] * 4096, [2] * 4096, 20_000)])
-def test_generate_host_equals_device_path(wn, torch, Ns, Rs, half):
-    # the second case moves 4096 x 20000 x 4 B > 256 MiB per call, so the
-    # values travel in several staging chunks with overlapped copies
+def test_generate_host_equals_device_path(wn, torch, Ns, Rs, half, pinned):
+    # pinned host memory: the kernel writes it directly; pageable memory: the
+    # values travel through staging buffers -- in the second case
+    # 4096 x 20000 x 4 B > 256 MiB per call, so in several chunks with
+    # overlapped copies
     n = len(Ns)
     seeds = list(range(5, 5 + n))
     dev = _gen(wn, torch, wn.wn_create_streams(Ns, Rs, seeds), 2 * half).cpu().view(n, 2 * half)
     h = wn.wn_create_streams(Ns, Rs, seeds)
-    host = torch.empty(n * half, dtype=torch.float32, pin_memory=True)
+    host = torch.empty(n * half, dtype=torch.float32, pin_memory=pinned)
     for c in range(2):  # consecutive calls continue each stream's sequence
         wn.wn_generate_host(host, half, h)
         torch.cuda.synchronize()
