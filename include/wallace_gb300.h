@@ -238,7 +238,21 @@ wn_status wn_set_cuda_stream(wn_stream *s, void *cuda_stream);
 wn_status wn_set_config(wn_stream *s, uint32_t quads_per_thread, uint32_t threads);
 
 /*
- * wn_autotune -- times every compiled launch shape that covers the handle's
+ * wn_set_config_ex -- wn_set_config with layout flags.  WN_CFG_IN_PLACE keeps
+ * each pool in one shared-memory buffer instead of two: a pass gathers all of
+ * its quadruples into registers, the compute warps meet at a barrier, and the
+ * results overwrite the pool.  This halves a CTA's shared memory, so that
+ * more CTAs share an SM (two with 16384-value pools instead of one), at the
+ * cost of one more barrier per pass.  The values are bit-identical to the
+ * two-buffer layout of the same shape.  Compiled for 16 quadruples per
+ * thread only; WN_EINVAL for unknown flags or shapes.  Launches of few
+ * streams that would take the latency mode use the ordinary kernel instead.
+ */
+#define WN_CFG_IN_PLACE 1u
+wn_status wn_set_config_ex(wn_stream *s, uint32_t quads_per_thread, uint32_t threads, uint32_t flags);
+
+/*
+ * wn_autotune -- times every compiled launch shape (and layout) that covers the handle's
  * pools on a saved copy of its state, generating `count` values per stream as
  * `dtype`, and keeps the fastest for later calls (the streams' sequences are
  * unaffected: the state is restored afterwards).  The chosen shape is
@@ -252,6 +266,10 @@ wn_status wn_autotune(wn_stream *s, uint64_t count, wn_dtype dtype, void *cuda_s
 
 /* wn_get_config -- the launch shape the next generate call will use. */
 wn_status wn_get_config(const wn_stream *s, uint32_t *quads_per_thread, uint32_t *threads);
+
+/* wn_get_config_ex -- the same and its layout flags (WN_CFG_IN_PLACE); any
+ * output pointer may be NULL. */
+wn_status wn_get_config_ex(const wn_stream *s, uint32_t *quads_per_thread, uint32_t *threads, uint32_t *flags);
 
 /* wn_num_streams -- number of streams in the handle (0 for NULL). */
 uint32_t wn_num_streams(const wn_stream *s);

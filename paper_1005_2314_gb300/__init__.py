@@ -24,12 +24,14 @@ __all__ = [
     "WN_F32", "WN_BF16", "WN_F16", "WnError",
     "wn_create", "wn_create_streams", "wn_create_ex", "WN_CHI2", "WN_RESERVE", "WN_UPDATE", "wn_destroy", "wn_generate", "wn_generate_ex",
     "wn_generate_host",
-    "wn_set_cuda_stream", "wn_set_config", "wn_get_config", "wn_autotune", "wn_gbm", "wn_generate_batch",
+    "wn_set_cuda_stream", "wn_set_config", "wn_get_config", "wn_set_config_ex", "wn_get_config_ex",
+    "WN_CFG_IN_PLACE", "wn_autotune", "wn_gbm", "wn_generate_batch",
     "wn_autotune_batch", "wn_generate_batch_noalloc", "wn_num_streams", "wn_get_pool", "wn_get_state",
     "wn_rng_draws", "wn_boxmuller", "wn_save", "wn_load", "wn_last_error", "library_path", "load",
 ]
 
 WN_F32, WN_BF16, WN_F16 = 0, 1, 2
+WN_CFG_IN_PLACE = 1
 WN_OK, WN_EINVAL, WN_ENOMEM, WN_ECUDA, WN_ETIMEOUT = 0, 1, 2, 3, 4
 _STATUS = {1: "WN_EINVAL", 2: "WN_ENOMEM", 3: "WN_ECUDA", 4: "WN_ETIMEOUT"}
 
@@ -61,6 +63,8 @@ def _load() -> ctypes.CDLL:
         "wn_set_cuda_stream": (_i, [_p, _p]),
         "wn_set_config": (_i, [_p, _u32, _u32]),
         "wn_get_config": (_i, [_p, _p, _p]),
+        "wn_set_config_ex": (_i, [_p, _u32, _u32, _u32]),
+        "wn_get_config_ex": (_i, [_p, _p, _p, _p]),
         "wn_autotune": (_i, [_p, _u64, _i, _p, _p, _p]),
         "wn_generate_batch": (_i, [_p, _p, _p, _p, _i, _i, _p]),
         "wn_autotune_batch": (_i, [_p, _p, _p, _p, _i, _p]),
@@ -249,6 +253,19 @@ def wn_get_config(h: Handle) -> tuple[int, int]:
     t = ctypes.c_uint32()
     _check(_L().wn_get_config(h.ptr, ctypes.addressof(q), ctypes.addressof(t)), "wn_get_config")
     return q.value, t.value
+
+
+def wn_set_config_ex(h: Handle, quads_per_thread: int, threads: int, flags: int = 0) -> None:
+    """wn_set_config with layout flags (WN_CFG_IN_PLACE: one pool buffer per CTA)."""
+    _check(_L().wn_set_config_ex(h.ptr, quads_per_thread, threads, flags), "wn_set_config_ex")
+
+
+def wn_get_config_ex(h: Handle) -> tuple[int, int, int]:
+    """(quadruples per thread, compute threads, layout flags) of the next generate call."""
+    q, t, f = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    _check(_L().wn_get_config_ex(h.ptr, ctypes.addressof(q), ctypes.addressof(t), ctypes.addressof(f)),
+           "wn_get_config_ex")
+    return q.value, t.value, f.value
 
 
 def wn_autotune(h: Handle, count: int, dtype: int = WN_F32, cuda_stream=None) -> tuple[int, int]:

@@ -185,7 +185,7 @@ using wn::LaunchCfg;
 bool cfg_ok(const LaunchCfg &c, uint32_t n_max)
 {
     bool compiled = false;
-    for (const auto &k : wn::kShapes) compiled |= (k[0] == c.qt && k[1] == c.maxt);
+    for (const auto &k : wn::kShapes) compiled |= (k[0] == c.qt && k[1] == c.maxt && k[3] == c.ip);
     return compiled && c.threads >= 32 && c.threads % 32 == 0 && c.threads + 32 <= (uint32_t)c.maxt &&
            (uint64_t)c.threads * c.qt >= n_max / 4;
 }
@@ -211,7 +211,14 @@ LaunchCfg pick_cfg(uint32_t n_max)
 // 8192 keep the ordinary kernel).
 bool fits_latency(const LaunchCfg &c, uint32_t n_max)
 {
-    return cfg_ok(c, n_max) && c.threads + 64 <= (uint32_t)c.maxt;
+    return !c.ip && cfg_ok(c, n_max) && c.threads + 64 <= (uint32_t)c.maxt;
+}
+
+// Dynamic shared memory of a launch of shape c over pools of up to n values
+// and up to r passes per block: one pool buffer in place, else two.
+size_t cfg_smem(const wn_stream *s, const LaunchCfg &c, uint32_t n, uint32_t r)
+{
+    return c.ip ? wn::gen_smem_bytes_ip(n, r) : wn::gen_smem_bytes(s->smem_base, n, r);
 }
 
 bool latency_default(uint32_t n_max, LaunchCfg &out)
@@ -220,7 +227,7 @@ bool latency_default(uint32_t n_max, LaunchCfg &out)
     const uint32_t t = nq >= 128 ? 128u : std::max(32u, (nq + 31u) / 32u * 32u);
     const int qt = (int)std::max(1u, nq / t);
     for (const auto &k : wn::kShapes) {
-        const LaunchCfg c{k[0], k[1], t};
+        const LaunchCfg c{k[0], k[1], t, k[3]};
         if (k[0] == qt && fits_latency(c, n_max)) {
             out = c;
             return true;
@@ -253,10 +260,10 @@ wn_status launch_generate(wn_stream *s, void *out, uint64_t count, uint32_t warm
     a.n_max = s->n_max;
     a.r_max = s->r_max;
     a.warmup_blocks = warmup;
-    const size_t smem = wn::gen_smem_bytes(s->smem_base, s->n_max, s->r_max);
     cudaError_t e;
     LaunchCfg lc;
     if (warmup == 0 && count > 0 && latency_cfg_for(s, lc)) {
+        const size_t smem = wn::gen_smem_bytes(s->smem_base, s->n_max, s->r_max);
         const bool full = s->uniform_N && (uint64_t)lc.threads * lc.qt == s->n_max / 4;
         switch (dt) {
         case WN_F32: e = wn::launch_latency_f32(a, lc, full, smem, cs); break;
@@ -268,6 +275,7 @@ wn_status launch_generate(wn_stream *s, void *out, uint64_t count, uint32_t warm
         return WN_OK;
     }
     const LaunchCfg c = s->has_cfg ? s->cfg : pick_cfg(s->n_max);
+    const size_t smem = cfg_smem(s, c, s->n_max, s->r_max);
     // every stream's quadruples exactly fill the CTA: no per-quadruple checks
     const bool full = s->uniform_N && (uint64_t)c.threads * c.qt == s->n_max / 4;
     switch (dt) {
@@ -461,6 +469,7 @@ wn_status enqueue_batch(wn_stream *s, const std::vector<Group> &groups, void *ou
         }
         const LaunchCfg c = g.exclusive ? latency_cfg(g.N) : group_cfg(s, g.N);
         const bool full = (uint64_t)c.threads * c.qt == g.N / 4;
+        if (!g.exclusive) smem = cfg_smem(s, c, g.N, g.r_max);
         switch (dt) {
         case WN_F32: e = wn::launch_persist_f32(a, bq, c, full, s->var, smem, s->sms, b); break;
         case WN_BF16: e = wn::launch_persist_bf16(a, bq, c, full, s->var, smem, s->sms, b); break;
@@ -810,26 +819,35 @@ void wn_destroy(wn_stream *s)
     delete s;
 }
 
-wn_status wn_set_config(wn_stream *s, uint32_t quads_per_thread, uint32_t threads)
+wn_status wn_set_config_ex(wn_stream *s, uint32_t quads_per_thread, uint32_t threads, uint32_t flags)
 {
     if (!s) return fail(WN_EINVAL, "wn_set_config: NULL handle");
+    if (flags & ~(uint32_t)WN_CFG_IN_PLACE) return fail(WN_EINVAL, "wn_set_config_ex: unknown flags");
     if (quads_per_thread == 0 && threads == 0) {
         s->has_cfg = false;
         return WN_OK;
     }
-    // the instantiation with the smallest thread bound that admits `threads`
+    // the instantiation of the asked layout with the smallest thread bound
+    // that admits `threads`
+    const int ip = (flags & WN_CFG_IN_PLACE) ? 1 : 0;
     LaunchCfg best{0, 0, threads};
     for (const auto &k : wn::kShapes) {
-        LaunchCfg c{k[0], k[1], threads};
-        if (k[0] == (int)quads_per_thread && cfg_ok(c, s->n_max) && (best.qt == 0 || k[1] < best.maxt)) best = c;
+        LaunchCfg c{k[0], k[1], threads, k[3]};
+        if (k[0] == (int)quads_per_thread && k[3] == ip && cfg_ok(c, s->n_max) && (best.qt == 0 || k[1] < best.maxt))
+            best = c;
     }
     if (best.qt == 0)
         return fail(WN_EINVAL, "wn_set_config: no compiled configuration with " + std::to_string(quads_per_thread) +
-                                   " quadruples per thread and " + std::to_string(threads) +
-                                   " threads covers pool " + std::to_string(s->n_max));
+                                   " quadruples per thread and " + std::to_string(threads) + " threads" +
+                                   (ip ? " (in-place layout)" : "") + " covers pool " + std::to_string(s->n_max));
     s->cfg = best;
     s->has_cfg = true;
     return WN_OK;
+}
+
+wn_status wn_set_config(wn_stream *s, uint32_t quads_per_thread, uint32_t threads)
+{
+    return wn_set_config_ex(s, quads_per_thread, threads, 0);
 }
 
 wn_status wn_autotune(wn_stream *s, uint64_t count, wn_dtype dtype, void *cuda_stream, uint32_t *quads_per_thread,
@@ -859,12 +877,12 @@ wn_status wn_autotune(wn_stream *s, uint64_t count, wn_dtype dtype, void *cuda_s
     const uint32_t nq = s->n_max / 4;
     for (const auto &k : wn::kShapes)
         for (uint32_t t = 32; t + 32 <= (uint32_t)k[1]; t += 32) {
-            LaunchCfg c{k[0], k[1], t};
+            LaunchCfg c{k[0], k[1], t, k[3]};
             const uint64_t slots = (uint64_t)t * k[0];
             if (cfg_ok(c, s->n_max) && slots < 2ull * nq + 32ull * k[0]) {
-                bool dup = false;  // same (qt, threads) under a larger bound
+                bool dup = false;  // same (qt, threads, layout) under a larger bound
                 for (auto &o : cand)
-                    if (o.qt == c.qt && o.threads == c.threads) dup = true;
+                    if (o.qt == c.qt && o.threads == c.threads && o.ip == c.ip) dup = true;
                 if (!dup) cand.push_back(c);
             }
         }
@@ -944,13 +962,19 @@ wn_status wn_autotune(wn_stream *s, uint64_t count, wn_dtype dtype, void *cuda_s
     return WN_OK;
 }
 
-wn_status wn_get_config(const wn_stream *s, uint32_t *quads_per_thread, uint32_t *threads)
+wn_status wn_get_config_ex(const wn_stream *s, uint32_t *quads_per_thread, uint32_t *threads, uint32_t *flags)
 {
     if (!s) return fail(WN_EINVAL, "wn_get_config: NULL handle");
     const LaunchCfg c = s->has_cfg ? s->cfg : pick_cfg(s->n_max);
     if (quads_per_thread) *quads_per_thread = (uint32_t)c.qt;
     if (threads) *threads = c.threads;
+    if (flags) *flags = c.ip ? (uint32_t)WN_CFG_IN_PLACE : 0u;
     return WN_OK;
+}
+
+wn_status wn_get_config(const wn_stream *s, uint32_t *quads_per_thread, uint32_t *threads)
+{
+    return wn_get_config_ex(s, quads_per_thread, threads, nullptr);
 }
 
 wn_status wn_set_cuda_stream(wn_stream *s, void *cuda_stream)
@@ -1128,7 +1152,7 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
         LaunchCfg best = pick_cfg(g.N);
         for (const auto &k : wn::kShapes)
             for (uint32_t t = 32; t + 32 <= (uint32_t)k[1] && e == cudaSuccess; t += 32) {
-                LaunchCfg c{k[0], k[1], t};
+                LaunchCfg c{k[0], k[1], t, k[3]};
                 if (!cfg_ok(c, g.N) || (uint64_t)t * k[0] != nq) continue;  // full shapes only
                 s->group_cfg[g.N] = c;
                 std::vector<Group> one(1, g);
@@ -1139,7 +1163,7 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
                     if (e == cudaSuccess) e = cudaEventRecord(e0, cs);
                     if (e == cudaSuccess) {
                         const bool full = true;
-                        const size_t smem = wn::gen_smem_bytes(s->smem_base, g.N, g.r_max);
+                        const size_t smem = cfg_smem(s, c, g.N, g.r_max);
                         wn::GenArgs a{s->d_hdr, s->d_pools, out, 0, 0, g.len, g.N, g.r_max, 0};
                         wn::BatchArgs bq{s->d_border + g.start, s->d_boffsets, s->d_bcounts, g.len, s->d_queue};
                         switch (dtype) {
@@ -1264,7 +1288,7 @@ wn_status wn_generate_batch_noalloc(void *out, const uint64_t *counts, const uin
         wn::BatchArgs bq{d_order + start[g], d_offsets, d_counts, cnt[g], d_counters + g};
         const LaunchCfg c = group_cfg(s, N);
         const bool full = (uint64_t)c.threads * c.qt == N / 4;
-        const size_t smem = wn::gen_smem_bytes(s->smem_base, N, rmax[g]);
+        const size_t smem = cfg_smem(s, c, N, rmax[g]);
         cudaError_t e;
         switch (dtype) {
         case WN_F32: e = wn::launch_persist_f32(a, bq, c, full, s->var, smem, s->sms, cs); break;

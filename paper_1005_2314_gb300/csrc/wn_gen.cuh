@@ -54,17 +54,24 @@ struct GenArgs {
 };
 
 // Launch shape: `threads` compute threads (plus the control warp) each owning
-// `qt` quadruples; `maxt` is the instantiation's thread bound.
+// `qt` quadruples; `maxt` is the instantiation's thread bound; `ip` selects
+// the in-place pool layout (one pool buffer instead of two; see run_stream).
 struct LaunchCfg {
     int qt;
     int maxt;
     uint32_t threads;
+    int ip = 0;
 };
 
 // Compiled shapes {quadruples per thread, thread bound (compute threads + 32),
-// minimum resident CTAs per SM (caps registers)}.
-constexpr int kShapes[][3] = {{1, 1024, 1}, {2, 544, 2}, {4, 288, 4}, {8, 160, 4}, {8, 544, 1}, {16, 288, 1}};
+// minimum resident CTAs per SM (caps registers), in-place pool}.  The
+// in-place shape halves the pool's shared memory, so that two CTAs with
+// 16384-value pools share an SM where the two-buffer layout fits one.
+constexpr int kShapes[][4] = {{1, 1024, 1, 0}, {2, 544, 2, 0}, {4, 288, 4, 0}, {8, 160, 4, 0},
+                              {8, 544, 1, 0},  {16, 288, 1, 0}, {16, 288, 2, 1}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+// Launcher switch key of a shape.
+constexpr int shape_key(int qt, int maxt, int ip) { return (ip * 100 + qt) * 10000 + maxt; }
 
 // Stream state the control warp keeps in shared memory between blocks.
 struct CtlState {
@@ -112,6 +119,14 @@ __host__ __device__ inline size_t gen_smem_bytes(uint32_t base, uint32_t n_max, 
 {
     return (size_t)pool_window(base, n_max, r_max) + 8 * (size_t)n_max - base;
 }
+// The in-place layout: one pool buffer right after the small part (a 16-byte
+// multiple); gather addresses are then offset + buffer (the add folds into
+// the shared load's address) instead of the OR of an aligned window.
+__host__ __device__ inline uint32_t pool_window_ip(uint32_t base, uint32_t r_max) { return base + small_bytes(r_max); }
+__host__ __device__ inline size_t gen_smem_bytes_ip(uint32_t n_max, uint32_t r_max)
+{
+    return (size_t)small_bytes(r_max) + 4 * (size_t)n_max;
+}
 
 // --- shared-memory and packed-FP32 primitives ------------------------------
 extern __shared__ __align__(16) unsigned char wn_smem[];
@@ -152,6 +167,9 @@ __device__ __forceinline__ void sts1(uint32_t a, float v) { asm volatile("st.sha
 // and reserved slot (kBarDone: the compute warps arrive, they wait).  An
 // arrive never waits; the writes before it are fenced for the waiting side.
 constexpr uint32_t kBarPass = 1, kBarReady = 2, kBarDone = 3;
+// In-place layout: the compute warps finish every gather of a pass before any
+// of them overwrites the pool (kBarGather, among themselves).
+constexpr uint32_t kBarGather = 4;
 __device__ __forceinline__ void bar_wait(uint32_t id, uint32_t n)
 {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
@@ -304,12 +322,19 @@ struct GbmArgs {
 // HAND (latency mode): instead of the nsync barriers, the owner of slot N-1
 // stores its value at window address rsv and the compute warps take the
 // scale from the control warps at kBarReady (nthr threads: the whole CTA).
-template <int QT, bool FINAL, bool FULL, int EMIT, int A, typename OutT, bool ROT, bool HAND = false>
+//
+// IP (in-place layout, rd == wr): addresses are offset + rd, the compute
+// warps (nthr threads) meet at kBarGather between their gathers and their
+// stores, and the final pass also stores slot N-1 at rsv (the control warp
+// reads the reserved value there, never from the pool being overwritten).
+template <int QT, bool FINAL, bool FULL, int EMIT, int A, typename OutT, bool ROT, bool HAND = false,
+          bool IP = false>
 __device__ __forceinline__ void pass_quads(uint32_t rd, uint32_t wr, uint32_t tab, uint32_t q0, uint32_t lane,
                                            uint32_t m4, uint32_t half, uint32_t nq, float2 &part, int nsync,
                                            OutT *__restrict__ ob, const float *sc_ptr, uint32_t n,
                                            float2 (&acc)[QT][2], uint32_t rsv = 0, uint32_t nthr = 0)
 {
+    static_assert(!(HAND && IP), "the latency mode keeps two pool buffers");
     const uint4 P = lds4u(tab);
     const float4 sg = lds4(tab + 16u + 16u * (lane & 15u));
     const float2 m01 = make_float2(sg.x, sg.y), m23 = make_float2(sg.z, sg.w);
@@ -320,16 +345,25 @@ __device__ __forceinline__ void pass_quads(uint32_t rd, uint32_t wr, uint32_t ta
     for (int j = 0; j < QT; ++j) {
         if (FULL || q0 + 32u * j < nq) {
             const uint32_t B = B0 + (uint32_t)j * P.w;
-            const uint32_t p0 = (B & m4) | rd;
-            const uint32_t p1 = ((B + P.z) & m4) | rd;
-            a[j][0] = lds(p0);
-            a[j][2] = lds(p0 ^ half);
-            a[j][1] = lds(p1);
-            a[j][3] = lds(p1 ^ half);
+            if (IP) {
+                const uint32_t o0 = B & m4, o1 = (B + P.z) & m4;
+                a[j][0] = lds(o0 + rd);
+                a[j][2] = lds((o0 ^ half) + rd);
+                a[j][1] = lds(o1 + rd);
+                a[j][3] = lds((o1 ^ half) + rd);
+            } else {
+                const uint32_t p0 = (B & m4) | rd;
+                const uint32_t p1 = ((B + P.z) & m4) | rd;
+                a[j][0] = lds(p0);
+                a[j][2] = lds(p0 ^ half);
+                a[j][1] = lds(p1);
+                a[j][3] = lds(p1 ^ half);
+            }
         } else {
             a[j][0] = a[j][1] = a[j][2] = a[j][3] = 0.f;
         }
     }
+    if (IP) bar_wait(kBarGather, nthr);  // the pool is read: it may now be overwritten
     float2 y[QT][2];
 #pragma unroll
     for (int j = 0; j < QT; ++j) {
@@ -349,7 +383,7 @@ __device__ __forceinline__ void pass_quads(uint32_t rd, uint32_t wr, uint32_t ta
         if (FULL || q < nq) {
             sts4(wr + 16u * q, y[j][0], y[j][1]);
             if (FINAL) part = ffma2(y[j][0], y[j][0], ffma2(y[j][1], y[j][1], part));
-            if (FINAL && HAND && (!FULL || j == QT - 1) && q + 1u == nq) sts1(rsv, y[j][1].y);  // slot N-1
+            if (FINAL && (HAND || IP) && (!FULL || j == QT - 1) && q + 1u == nq) sts1(rsv, y[j][1].y);  // slot N-1
         }
     }
     if (FINAL && HAND) bar_wait(kBarReady, nthr);
@@ -439,11 +473,12 @@ __device__ __forceinline__ void pass_quads(uint32_t rd, uint32_t wr, uint32_t ta
 // pass per block the final pass is also the first, so it waits for the scale
 // at a mid-phase barrier.
 // ---------------------------------------------------------------------------
-template <int QT, bool FULL, typename OutT, bool GBM, bool VAR, bool ROT>
+template <int QT, bool FULL, typename OutT, bool GBM, bool VAR, bool ROT, bool IP = false>
 __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__restrict__ pool_g,
                                            OutT *__restrict__ out, uint64_t out_off, uint64_t count,
                                            bool store, uint32_t n_max, uint32_t r_max, const GbmArgs &gbm)
 {
+    static_assert(!(GBM && IP), "the GBM consumer keeps its path sums in the second pool buffer");
     unsigned char *smem = wn_smem;
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const bool control = (warp == 0);
@@ -451,8 +486,8 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
     const uint32_t base = smem_base();
     uint32_t dyn;
     asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
-    const uint32_t W0 = pool_window(base, n_max, r_max);
-    if (W0 + 8u * n_max > base + dyn) {  // layout does not fit: flag and do nothing
+    const uint32_t W0 = IP ? pool_window_ip(base, r_max) : pool_window(base, n_max, r_max);
+    if (W0 + (IP ? 4u : 8u) * n_max > base + dyn) {  // layout does not fit: flag and do nothing
         if (tid == 0) h->flags |= 1u;
         return;
     }
@@ -460,8 +495,10 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
     CtlState *ctl = reinterpret_cast<CtlState *>(smem + 256);
     PassTab *tabs = reinterpret_cast<PassTab *>(smem + 256 + sizeof(CtlState));  // [2][r_max]
     const uint32_t tabs_s = base + 256u + (uint32_t)sizeof(CtlState);
-    const uint32_t bsz = 4u * n_max;  // bytes per buffer; buffer i at window W0 + i bsz
+    // bytes per buffer; buffer i at window W0 + i bsz (in place: one buffer)
+    const uint32_t bsz = IP ? 0u : 4u * n_max;
     const uint32_t nwc = (blockDim.x >> 5) - 1u;  // compute warps
+    const uint32_t ncomp = blockDim.x - 32u;
     const uint32_t q0 = (warp - 1u) * 32u * QT + lane;
     const uint32_t m4 = 4u * N - 1u, half = 2u * N;
 
@@ -500,6 +537,7 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
     if (store)
         for (uint64_t i = tid; i < n0; i += blockDim.x)
             out[i] = to_out<OutT>(sc_prev * lds(W0 + 4u * (uint32_t)(k0 + i)));
+    if (IP && store && n0 > 0) __syncthreads();  // the control warp's reads precede the first pass's stores
 
     // Control warp: FP64 sum of the compute warps' partial sums of squares of
     // parity `par` (the pool at the end of that block).
@@ -513,7 +551,9 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
     // Control warp: block b's scale sqrt(S / sum of squares) (Section 5.5).
     // rslot is the window address of a pool's slot N-1 (unscaled): the
     // previous block's (fastnorm2: its reserved value times that block's
-    // scale) or, with `late`, this block's own (fastnorm: renormalised).
+    // scale; in place, the copy the final pass left in the partial-sum array,
+    // since the first pass may already be overwriting the pool) or, with
+    // `late`, this block's own (fastnorm: renormalised).
     auto form_scale = [&](uint64_t b, uint32_t rslot) {
         const double ss = (b == 0) ? ctl->sumsq : sum_partials((uint32_t)((b - 1) & 1));
         const float invNf = 1.0f / (float)N;  // exact: N is a power of two
@@ -552,7 +592,7 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
                 // second (the final pass, which carries the stores): the two
                 // serial chains then each overlap a phase of compute work
                 if (p == 0 && !late) {
-                    form_scale(b, rd + 4u * (N - 1u));
+                    form_scale(b, IP ? base + 4u * ((uint32_t)((b - 1) & 1) * 32u + 31u) : rd + 4u * (N - 1u));
                     if (one_pass) __syncthreads();  // pairs with the final pass's mid-phase barrier
                 }
                 if (p == (one_pass ? 0u : 1u) && b + 1 < nrun)
@@ -564,41 +604,42 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
                 }
             } else if (p + 1 < R) {
                 float2 part;
-                pass_quads<QT, false, FULL, EMIT_NONE, 0, OutT, ROT>(rd, wr, tp, q0, lane, m4, half, nq, part, 0,
-                                                               nullptr, nullptr, 0, acc);
+                pass_quads<QT, false, FULL, EMIT_NONE, 0, OutT, ROT, false, IP>(
+                    rd, wr, tp, q0, lane, m4, half, nq, part, 0, nullptr, nullptr, 0, acc, 0, ncomp);
             } else {
                 float2 part = make_float2(0.f, 0.f);
                 const float *scp = &ctl->sc[b & 1];
+                const uint32_t rsv = base + 4u * ((uint32_t)(b & 1) * 32u + 31u);  // in place: slot N-1's copy
                 const bool emit = (dec == 1) || (dc + 1 == dec);  // decimation: a block to return
                 const bool whole = ((dec == 1 ? b : e) + 1 < nb) || tail == 0;
                 if (GBM && emit) {
-                    pass_quads<QT, true, FULL, EMIT_GBM, 0, OutT, ROT>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                 nsync, ob, scp, 0, acc);
+                    pass_quads<QT, true, FULL, EMIT_GBM, 0, OutT, ROT, false, IP>(rd, wr, tp, q0, lane, m4, half, nq, part,
+                                                                 nsync, ob, scp, 0, acc, rsv, ncomp);
                 } else if (!store || !emit) {
-                    pass_quads<QT, true, FULL, EMIT_NONE, 0, OutT, ROT>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                  0, ob, scp, 0, acc);
+                    pass_quads<QT, true, FULL, EMIT_NONE, 0, OutT, ROT, false, IP>(rd, wr, tp, q0, lane, m4, half, nq, part,
+                                                                  0, ob, scp, 0, acc, rsv, ncomp);
                     if (nsync > 0) __syncthreads();
                     if (nsync > 1) __syncthreads();
                 } else if (!whole) {
-                    pass_quads<QT, true, FULL, EMIT_PART, 0, OutT, ROT>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                  nsync, ob, scp, (uint32_t)tail, acc);
+                    pass_quads<QT, true, FULL, EMIT_PART, 0, OutT, ROT, false, IP>(rd, wr, tp, q0, lane, m4, half, nq, part,
+                                                                  nsync, ob, scp, (uint32_t)tail, acc, rsv, ncomp);
                 } else {
                     switch (a) {
                     case 0:
-                        pass_quads<QT, true, FULL, EMIT_WHOLE, 0, OutT, ROT>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                       nsync, ob, scp, 0, acc);
+                        pass_quads<QT, true, FULL, EMIT_WHOLE, 0, OutT, ROT, false, IP>(rd, wr, tp, q0, lane, m4, half, nq, part,
+                                                                       nsync, ob, scp, 0, acc, rsv, ncomp);
                         break;
                     case 1:
-                        pass_quads<QT, true, FULL, EMIT_WHOLE, 1, OutT, ROT>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                       nsync, ob, scp, 0, acc);
+                        pass_quads<QT, true, FULL, EMIT_WHOLE, 1, OutT, ROT, false, IP>(rd, wr, tp, q0, lane, m4, half, nq, part,
+                                                                       nsync, ob, scp, 0, acc, rsv, ncomp);
                         break;
                     case 2:
-                        pass_quads<QT, true, FULL, EMIT_WHOLE, 2, OutT, ROT>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                       nsync, ob, scp, 0, acc);
+                        pass_quads<QT, true, FULL, EMIT_WHOLE, 2, OutT, ROT, false, IP>(rd, wr, tp, q0, lane, m4, half, nq, part,
+                                                                       nsync, ob, scp, 0, acc, rsv, ncomp);
                         break;
                     default:
-                        pass_quads<QT, true, FULL, EMIT_WHOLE, 3, OutT, ROT>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                       nsync, ob, scp, 0, acc);
+                        pass_quads<QT, true, FULL, EMIT_WHOLE, 3, OutT, ROT, false, IP>(rd, wr, tp, q0, lane, m4, half, nq, part,
+                                                                       nsync, ob, scp, 0, acc, rsv, ncomp);
                         break;
                     }
                 }
@@ -847,8 +888,9 @@ __global__ void __launch_bounds__(MAXT, MINB) latency_kernel(GenArgs a)
 }
 
 // FULL: every stream of the launch has exactly (blockDim.x - 32) * QT
-// quadruples, so no quadruple index needs a bounds check.
-template <int QT, int MAXT, int MINB, bool FULL, typename OutT, bool VAR>
+// quadruples, so no quadruple index needs a bounds check.  IP: the in-place
+// pool layout.
+template <int QT, int MAXT, int MINB, bool FULL, typename OutT, bool VAR, bool IP = false>
 __global__ void __launch_bounds__(MAXT, MINB) generate_kernel(GenArgs a)
 {
     StreamHdr *h = a.hdr + blockIdx.x;
@@ -858,11 +900,11 @@ __global__ void __launch_bounds__(MAXT, MINB) generate_kernel(GenArgs a)
     OutT *out = a.out ? reinterpret_cast<OutT *>(a.out) + off : nullptr;
     const GbmArgs none{};
     if (VAR && var_rotation(h->variant))
-        run_stream<QT, FULL, OutT, false, VAR, true>(h, a.pools + h->pool_off, out, off, count, a.warmup_blocks == 0,
-                                                     a.n_max, a.r_max, none);
+        run_stream<QT, FULL, OutT, false, VAR, true, IP>(h, a.pools + h->pool_off, out, off, count,
+                                                         a.warmup_blocks == 0, a.n_max, a.r_max, none);
     else
-        run_stream<QT, FULL, OutT, false, VAR, false>(h, a.pools + h->pool_off, out, off, count, a.warmup_blocks == 0,
-                                                      a.n_max, a.r_max, none);
+        run_stream<QT, FULL, OutT, false, VAR, false, IP>(h, a.pools + h->pool_off, out, off, count,
+                                                          a.warmup_blocks == 0, a.n_max, a.r_max, none);
 }
 
 // The fused GBM consumer: every stream of the launch returns steps * ppg
@@ -894,7 +936,7 @@ struct BatchArgs {
 // the next stream from an atomic counter (longest first), returns that
 // stream's request, and claims again until the list is exhausted.  No CTA
 // waits on another.
-template <int QT, int MAXT, int MINB, bool FULL, typename OutT, bool VAR>
+template <int QT, int MAXT, int MINB, bool FULL, typename OutT, bool VAR, bool IP = false>
 __global__ void __launch_bounds__(MAXT, MINB) persist_kernel(GenArgs a, BatchArgs bq)
 {
     CtlState *ctl = reinterpret_cast<CtlState *>(wn_smem + 256);
@@ -910,22 +952,22 @@ __global__ void __launch_bounds__(MAXT, MINB) persist_kernel(GenArgs a, BatchArg
         const uint64_t off = bq.offsets[si];
         OutT *o = reinterpret_cast<OutT *>(a.out) + off;
         if (VAR && var_rotation(h->variant))
-            run_stream<QT, FULL, OutT, false, VAR, true>(h, a.pools + h->pool_off, o, off, bq.counts[si], true, a.n_max,
-                                                         a.r_max, none);
+            run_stream<QT, FULL, OutT, false, VAR, true, IP>(h, a.pools + h->pool_off, o, off, bq.counts[si], true,
+                                                             a.n_max, a.r_max, none);
         else
-            run_stream<QT, FULL, OutT, false, VAR, false>(h, a.pools + h->pool_off, o, off, bq.counts[si], true,
-                                                          a.n_max, a.r_max, none);
+            run_stream<QT, FULL, OutT, false, VAR, false, IP>(h, a.pools + h->pool_off, o, off, bq.counts[si], true,
+                                                              a.n_max, a.r_max, none);
     }
 }
 
-template <int QT, int MAXT, int MINB, typename OutT>
+template <int QT, int MAXT, int MINB, typename OutT, bool IP = false>
 cudaError_t launch_persist_shape(const GenArgs &a, const BatchArgs &bq, uint32_t threads, bool full, bool var,
                                  size_t smem, int sms, cudaStream_t cs)
 {
-    auto kern = full ? (var ? persist_kernel<QT, MAXT, MINB, true, OutT, true>
-                            : persist_kernel<QT, MAXT, MINB, true, OutT, false>)
-                     : (var ? persist_kernel<QT, MAXT, MINB, false, OutT, true>
-                            : persist_kernel<QT, MAXT, MINB, false, OutT, false>);
+    auto kern = full ? (var ? persist_kernel<QT, MAXT, MINB, true, OutT, true, IP>
+                            : persist_kernel<QT, MAXT, MINB, true, OutT, false, IP>)
+                     : (var ? persist_kernel<QT, MAXT, MINB, false, OutT, true, IP>
+                            : persist_kernel<QT, MAXT, MINB, false, OutT, false, IP>);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -944,13 +986,16 @@ template <typename OutT>
 cudaError_t launch_persist_t(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full, bool var,
                              size_t smem, int sms, cudaStream_t cs)
 {
-    switch (c.qt * 10000 + c.maxt) {
-    case 1 * 10000 + 1024: return launch_persist_shape<1, 1024, 1, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
-    case 2 * 10000 + 544: return launch_persist_shape<2, 544, 2, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
-    case 4 * 10000 + 288: return launch_persist_shape<4, 288, 4, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
-    case 8 * 10000 + 160: return launch_persist_shape<8, 160, 4, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
-    case 8 * 10000 + 544: return launch_persist_shape<8, 544, 1, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
-    case 16 * 10000 + 288: return launch_persist_shape<16, 288, 1, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
+    switch (shape_key(c.qt, c.maxt, c.ip)) {
+    case shape_key(1, 1024, 0): return launch_persist_shape<1, 1024, 1, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
+    case shape_key(2, 544, 0): return launch_persist_shape<2, 544, 2, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
+    case shape_key(4, 288, 0): return launch_persist_shape<4, 288, 4, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
+    case shape_key(8, 160, 0): return launch_persist_shape<8, 160, 4, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
+    case shape_key(8, 544, 0): return launch_persist_shape<8, 544, 1, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
+    case shape_key(16, 288, 0):
+        return launch_persist_shape<16, 288, 1, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
+    case shape_key(16, 288, 1):
+        return launch_persist_shape<16, 288, 2, OutT, true>(a, bq, c.threads, full, var, smem, sms, cs);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -971,13 +1016,13 @@ constexpr int kGbmShapes[][3] = {{1, 1024, 1}, {4, 288, 3}, {8, 544, 1}};
 cudaError_t launch_gbm(const GenArgs &a, const GbmArgs &g, const LaunchCfg &c, bool full, size_t smem,
                        cudaStream_t cs);
 
-template <int QT, int MAXT, int MINB, typename OutT>
+template <int QT, int MAXT, int MINB, typename OutT, bool IP = false>
 cudaError_t launch_shape(const GenArgs &a, uint32_t threads, bool full, bool var, size_t smem, cudaStream_t cs)
 {
-    auto kern = full ? (var ? generate_kernel<QT, MAXT, MINB, true, OutT, true>
-                            : generate_kernel<QT, MAXT, MINB, true, OutT, false>)
-                     : (var ? generate_kernel<QT, MAXT, MINB, false, OutT, true>
-                            : generate_kernel<QT, MAXT, MINB, false, OutT, false>);
+    auto kern = full ? (var ? generate_kernel<QT, MAXT, MINB, true, OutT, true, IP>
+                            : generate_kernel<QT, MAXT, MINB, true, OutT, false, IP>)
+                     : (var ? generate_kernel<QT, MAXT, MINB, false, OutT, true, IP>
+                            : generate_kernel<QT, MAXT, MINB, false, OutT, false, IP>);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -990,13 +1035,14 @@ cudaError_t launch_shape(const GenArgs &a, uint32_t threads, bool full, bool var
 template <typename OutT>
 cudaError_t launch_generate_t(const GenArgs &a, const LaunchCfg &c, bool full, bool var, size_t smem, cudaStream_t cs)
 {
-    switch (c.qt * 10000 + c.maxt) {
-    case 1 * 10000 + 1024: return launch_shape<1, 1024, 1, OutT>(a, c.threads, full, var, smem, cs);
-    case 2 * 10000 + 544: return launch_shape<2, 544, 2, OutT>(a, c.threads, full, var, smem, cs);
-    case 4 * 10000 + 288: return launch_shape<4, 288, 4, OutT>(a, c.threads, full, var, smem, cs);
-    case 8 * 10000 + 160: return launch_shape<8, 160, 4, OutT>(a, c.threads, full, var, smem, cs);
-    case 8 * 10000 + 544: return launch_shape<8, 544, 1, OutT>(a, c.threads, full, var, smem, cs);
-    case 16 * 10000 + 288: return launch_shape<16, 288, 1, OutT>(a, c.threads, full, var, smem, cs);
+    switch (shape_key(c.qt, c.maxt, c.ip)) {
+    case shape_key(1, 1024, 0): return launch_shape<1, 1024, 1, OutT>(a, c.threads, full, var, smem, cs);
+    case shape_key(2, 544, 0): return launch_shape<2, 544, 2, OutT>(a, c.threads, full, var, smem, cs);
+    case shape_key(4, 288, 0): return launch_shape<4, 288, 4, OutT>(a, c.threads, full, var, smem, cs);
+    case shape_key(8, 160, 0): return launch_shape<8, 160, 4, OutT>(a, c.threads, full, var, smem, cs);
+    case shape_key(8, 544, 0): return launch_shape<8, 544, 1, OutT>(a, c.threads, full, var, smem, cs);
+    case shape_key(16, 288, 0): return launch_shape<16, 288, 1, OutT>(a, c.threads, full, var, smem, cs);
+    case shape_key(16, 288, 1): return launch_shape<16, 288, 2, OutT, true>(a, c.threads, full, var, smem, cs);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1056,7 +1102,7 @@ template <typename OutT>
 cudaError_t launch_persist_lat_t(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full, size_t smem,
                                  int sms, cudaStream_t cs)
 {
-    if (c.threads + 64 > (uint32_t)c.maxt) return cudaErrorInvalidValue;
+    if (c.ip || c.threads + 64 > (uint32_t)c.maxt) return cudaErrorInvalidValue;  // two buffers, two control warps
     switch (c.qt * 10000 + c.maxt) {
     case 1 * 10000 + 1024: return launch_persist_lat_shape<1, 1024, 1, OutT>(a, bq, c.threads, full, smem, sms, cs);
     case 2 * 10000 + 544: return launch_persist_lat_shape<2, 544, 2, OutT>(a, bq, c.threads, full, smem, sms, cs);
@@ -1080,7 +1126,7 @@ cudaError_t launch_persist_lat_f16(const GenArgs &a, const BatchArgs &bq, const 
 template <typename OutT>
 cudaError_t launch_latency_t(const GenArgs &a, const LaunchCfg &c, bool full, size_t smem, cudaStream_t cs)
 {
-    if (c.threads + 64 > (uint32_t)c.maxt) return cudaErrorInvalidValue;
+    if (c.ip || c.threads + 64 > (uint32_t)c.maxt) return cudaErrorInvalidValue;  // two buffers, two control warps
     switch (c.qt * 10000 + c.maxt) {
     case 1 * 10000 + 1024: return launch_latency_shape<1, 1024, 1, OutT>(a, c.threads, full, smem, cs);
     case 2 * 10000 + 544: return launch_latency_shape<2, 544, 2, OutT>(a, c.threads, full, smem, cs);
