@@ -198,10 +198,14 @@ wn_status wn_generate_batch_noalloc(void *out, const uint64_t *counts, const uin
 /*
  * wn_autotune_batch -- picks, for each pool size of the batch described by
  * out/counts/offsets/dtype (as in wn_generate_batch), the compiled launch
- * shape whose persistent kernel serves that group fastest, timing each on a
- * saved copy of the state (the streams' sequences are unaffected; `out` is
- * overwritten with scratch values).  Later wn_generate_batch calls use the
- * chosen shapes.  Synchronous.
+ * shape (or the latency mode) whose persistent kernel serves that group
+ * fastest, timing each group alone; then times the whole batch with those
+ * shapes for several numbers of exclusive groups (the longest serial chains,
+ * one CTA per SM: none, 4, 8, ... up to a third of the SMs, or the
+ * estimate's rule) and keeps the fastest.  All timing runs on a saved copy of
+ * the state (the streams' sequences are unaffected; `out` is overwritten
+ * with scratch values).  Later wn_generate_batch calls use the choices.
+ * Synchronous.
  */
 wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *offsets, wn_stream *s,
                             wn_dtype dtype, void *cuda_stream);

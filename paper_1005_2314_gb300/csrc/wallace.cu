@@ -138,6 +138,9 @@ struct wn_stream {
     // every group whose pool size has a latency shape (2); 0: never.  The
     // batch tuner's choice per pool size (group_lat) overrides it.
     int batch_lat = 2;
+    // batches: how many of the longest serial chains get exclusive groups, as
+    // timed on the whole batch by wn_autotune_batch (-1: the estimate's rule)
+    int batch_crit = -1;
     std::map<uint32_t, bool> group_lat;
     // some stream runs a method variant (wn_create_ex, wn_load): use the
     // kernels that read StreamHdr::variant (the others compile the plain method)
@@ -339,8 +342,10 @@ LaunchCfg latency_cfg(uint32_t N)
 // about 400 + N/20 ns against 0.34 ps per value-pass over the machine --
 // would set the batch's length; up to a third of the SMs' worth of such
 // requests (longest first) get exclusive groups instead: one CTA per SM with
-// the lowest-latency shape, so that no other CTA shares their SM.
-std::vector<Group> plan_batch(const wn_stream *s, const uint64_t *counts, std::vector<uint32_t> &order)
+// the lowest-latency shape, so that no other CTA shares their SM.  After
+// wn_autotune_batch, `crit` (s->batch_crit) fixes how many of the longest
+// chains get them instead of the estimate's threshold.
+std::vector<Group> plan_batch(const wn_stream *s, const uint64_t *counts, std::vector<uint32_t> &order, int crit_k)
 {
     std::vector<double> chain(s->n);
     double thr = 0.0;
@@ -356,10 +361,10 @@ std::vector<Group> plan_batch(const wn_stream *s, const uint64_t *counts, std::v
     std::vector<char> crit(s->n, 0);
     std::map<uint32_t, std::vector<uint32_t>> by_n, crit_n;
     for (uint32_t i = 0; i < s->n; ++i) by_n[s->N[i]];
-    const uint32_t max_crit = (uint32_t)std::max(1, s->sms / 3);
+    const uint32_t max_crit = crit_k >= 0 ? (uint32_t)crit_k : (uint32_t)std::max(1, s->sms / 3);
     for (uint32_t k = 0; k < s->n && k < max_crit; ++k) {
         const uint32_t i = by_chain[k];
-        if (!(chain[i] > thr) || counts[i] == 0) break;
+        if ((crit_k < 0 && !(chain[i] > thr)) || counts[i] == 0) break;
         if (by_n.size() + crit_n.size() + (crit_n.count(s->N[i]) ? 0 : 1) > 16) break;  // one claim counter each
         crit[i] = 1;
         crit_n[s->N[i]].push_back(i);
@@ -1067,7 +1072,7 @@ wn_status wn_generate_batch(void *out, const uint64_t *counts, const uint64_t *o
     if (st != WN_OK) return st;
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(cuda_stream);
     std::vector<uint32_t> order;
-    const std::vector<Group> groups = plan_batch(s, counts, order);
+    const std::vector<Group> groups = plan_batch(s, counts, order, s->batch_crit);
     if (groups.size() > 16) return fail(WN_EINVAL, "wn_generate_batch: more than 16 pool sizes");
     if ((st = ensure_batch_buffers(s, groups.size())) != WN_OK) return st;
     const bool same = use_graph && s->gexec && s->g_out == out && s->g_dtype == (int)dtype &&
@@ -1119,7 +1124,7 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
     if (st != WN_OK) return st;
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(cuda_stream);
     std::vector<uint32_t> order;
-    const std::vector<Group> groups = plan_batch(s, counts, order);
+    const std::vector<Group> groups = plan_batch(s, counts, order, -1);
     if (groups.size() > 16) return fail(WN_EINVAL, "wn_autotune_batch: more than 16 pool sizes");
     if ((st = ensure_batch_buffers(s, groups.size())) != WN_OK) return st;
     WN_CU(cudaMemcpyAsync(s->d_bcounts, counts, sizeof(uint64_t) * s->n, cudaMemcpyHostToDevice, cs));
@@ -1215,6 +1220,43 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
         }
         chosen_lat[g.N] = lat;
     }
+    // Then the whole batch with the chosen shapes, for several numbers of
+    // exclusive chains (0 .. a third of the SMs, and the estimate's rule):
+    // the groups share the machine, which timing them alone cannot show.
+    int best_crit = -1;
+    if (e == cudaSuccess) {
+        for (auto &kv : chosen) s->group_cfg[kv.first] = kv.second;
+        for (auto &kv : chosen_lat) s->group_lat[kv.first] = kv.second;
+        const int third = std::max(1, s->sms / 3);
+        std::vector<int> ks = {-1, 0};
+        for (int k = 4; k < third; k *= 2) ks.push_back(k);
+        ks.push_back(third);
+        float best_ms = 1e30f;
+        for (int k : ks) {
+            std::vector<uint32_t> ord;
+            const std::vector<Group> gk = plan_batch(s, counts, ord, k);
+            if (gk.size() > 16) continue;
+            if ((st = ensure_batch_buffers(s, gk.size())) != WN_OK) break;
+            e = cudaMemcpyAsync(s->d_border, ord.data(), sizeof(uint32_t) * s->n, cudaMemcpyHostToDevice, cs);
+            float times[2] = {0.f, 0.f};
+            for (int rep = 0; rep < 3 && e == cudaSuccess && st == WN_OK; ++rep) {
+                e = restore();
+                if (e == cudaSuccess) e = cudaEventRecord(e0, cs);
+                if (e == cudaSuccess) st = enqueue_batch(s, gk, out, dtype, cs);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, cs);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) times[rep - 1] = ms;
+            }
+            if (e != cudaSuccess || st != WN_OK) break;
+            const float t_ms = std::min(times[0], times[1]);
+            if (t_ms < best_ms) {
+                best_ms = t_ms;
+                best_crit = k;
+            }
+        }
+    }
     if (e == cudaSuccess) e = restore();
     if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
     if (hdr_bak) cudaFree(hdr_bak);
@@ -1222,8 +1264,10 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (e != cudaSuccess) return cuda_fail("wn_autotune_batch", e);
+    if (st != WN_OK) return st;
     for (auto &kv : chosen) s->group_cfg[kv.first] = kv.second;
     for (auto &kv : chosen_lat) s->group_lat[kv.first] = kv.second;
+    s->batch_crit = best_crit;
     if (s->gexec) {  // a captured graph used the old shapes
         cudaGraphExecDestroy(s->gexec);
         s->gexec = nullptr;

@@ -613,33 +613,33 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
                 const bool emit = (dec == 1) || (dc + 1 == dec);  // decimation: a block to return
                 const bool whole = ((dec == 1 ? b : e) + 1 < nb) || tail == 0;
                 if (GBM && emit) {
-                    pass_quads<QT, true, FULL, EMIT_GBM, 0, OutT, ROT, false, IP>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                 nsync, ob, scp, 0, acc, rsv, ncomp);
+                    pass_quads<QT, true, FULL, EMIT_GBM, 0, OutT, ROT, false, IP>(
+                        rd, wr, tp, q0, lane, m4, half, nq, part, nsync, ob, scp, 0, acc, rsv, ncomp);
                 } else if (!store || !emit) {
-                    pass_quads<QT, true, FULL, EMIT_NONE, 0, OutT, ROT, false, IP>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                  0, ob, scp, 0, acc, rsv, ncomp);
+                    pass_quads<QT, true, FULL, EMIT_NONE, 0, OutT, ROT, false, IP>(
+                        rd, wr, tp, q0, lane, m4, half, nq, part, 0, ob, scp, 0, acc, rsv, ncomp);
                     if (nsync > 0) __syncthreads();
                     if (nsync > 1) __syncthreads();
                 } else if (!whole) {
-                    pass_quads<QT, true, FULL, EMIT_PART, 0, OutT, ROT, false, IP>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                  nsync, ob, scp, (uint32_t)tail, acc, rsv, ncomp);
+                    pass_quads<QT, true, FULL, EMIT_PART, 0, OutT, ROT, false, IP>(
+                        rd, wr, tp, q0, lane, m4, half, nq, part, nsync, ob, scp, (uint32_t)tail, acc, rsv, ncomp);
                 } else {
                     switch (a) {
                     case 0:
-                        pass_quads<QT, true, FULL, EMIT_WHOLE, 0, OutT, ROT, false, IP>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                       nsync, ob, scp, 0, acc, rsv, ncomp);
+                        pass_quads<QT, true, FULL, EMIT_WHOLE, 0, OutT, ROT, false, IP>(
+                            rd, wr, tp, q0, lane, m4, half, nq, part, nsync, ob, scp, 0, acc, rsv, ncomp);
                         break;
                     case 1:
-                        pass_quads<QT, true, FULL, EMIT_WHOLE, 1, OutT, ROT, false, IP>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                       nsync, ob, scp, 0, acc, rsv, ncomp);
+                        pass_quads<QT, true, FULL, EMIT_WHOLE, 1, OutT, ROT, false, IP>(
+                            rd, wr, tp, q0, lane, m4, half, nq, part, nsync, ob, scp, 0, acc, rsv, ncomp);
                         break;
                     case 2:
-                        pass_quads<QT, true, FULL, EMIT_WHOLE, 2, OutT, ROT, false, IP>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                       nsync, ob, scp, 0, acc, rsv, ncomp);
+                        pass_quads<QT, true, FULL, EMIT_WHOLE, 2, OutT, ROT, false, IP>(
+                            rd, wr, tp, q0, lane, m4, half, nq, part, nsync, ob, scp, 0, acc, rsv, ncomp);
                         break;
                     default:
-                        pass_quads<QT, true, FULL, EMIT_WHOLE, 3, OutT, ROT, false, IP>(rd, wr, tp, q0, lane, m4, half, nq, part,
-                                                                       nsync, ob, scp, 0, acc, rsv, ncomp);
+                        pass_quads<QT, true, FULL, EMIT_WHOLE, 3, OutT, ROT, false, IP>(
+                            rd, wr, tp, q0, lane, m4, half, nq, part, nsync, ob, scp, 0, acc, rsv, ncomp);
                         break;
                     }
                 }
@@ -987,7 +987,8 @@ cudaError_t launch_persist_t(const GenArgs &a, const BatchArgs &bq, const Launch
                              size_t smem, int sms, cudaStream_t cs)
 {
     switch (shape_key(c.qt, c.maxt, c.ip)) {
-    case shape_key(1, 1024, 0): return launch_persist_shape<1, 1024, 1, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
+    case shape_key(1, 1024, 0):
+        return launch_persist_shape<1, 1024, 1, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
     case shape_key(2, 544, 0): return launch_persist_shape<2, 544, 2, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
     case shape_key(4, 288, 0): return launch_persist_shape<4, 288, 4, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
     case shape_key(8, 160, 0): return launch_persist_shape<8, 160, 4, OutT>(a, bq, c.threads, full, var, smem, sms, cs);

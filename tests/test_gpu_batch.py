@@ -105,13 +105,13 @@ def test_uneven_recipe_scaled_down(wn):
     _check(got, N[pick], R[pick], seeds[pick], counts[pick], offsets[pick])
 
 
-def test_latency_mode_is_bit_identical_to_the_ordinary_kernel(wn):
+@pytest.mark.parametrize("R", [1, 2, 3])
+def test_latency_mode_is_bit_identical_to_the_ordinary_kernel(wn, R):
     # Few streams run in the latency mode (two control warps, named-barrier
-    # handoffs); many streams run the ordinary kernel.  With the same
-    # compute-warp layout the arithmetic is the same, so a stream's values
-    # must agree bit for bit.
+    # handoffs); many streams run the ordinary kernel.  With the same compute-warp layout the arithmetic is the same,
+    # so a stream's values must agree bit for bit.
     import torch
-    N, R, shape = 1024, 2, (2, 128)
+    N, shape = 1024, (2, 128)
     n_many = 200  # more than half the SMs: the ordinary kernel
     many = wn.wn_create_streams([N] * n_many, [R] * n_many, list(range(1, n_many + 1)))
     wn.wn_set_config(many, *shape)
