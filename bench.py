@@ -15,6 +15,11 @@ FP64 CPU oracle timed on the host's cores on a bounded sample (cpu_baseline).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+--kernel-only times the generate steps alone (for ncu captures); with it,
+--pool/--passes/--dtype/--in-place select another workload of the kernel
+(e.g. the 16-bit precision workload's pools: --pool 16384 --passes 3
+--dtype bf16).
+
 For N > 1 run under torch.distributed.run; ranks shard streams (weak scaling)
 and only the timing is reduced (max over ranks).
 """
@@ -41,18 +46,22 @@ HDR_BYTES = 96
 KERNEL_SOURCES = ("wn_gen.cuh", "wn_device.cuh")
 
 
-def _workload(streams, per_stream):
-    return (f"many_streams: {streams} streams x pool N={POOL_N}, R={PASSES_R} passes/block, "
-            f"seeds SplitMix64(1..{streams}), {per_stream} FP32 variates per stream per step")
+ESIZE = {"f32": 4, "bf16": 2, "f16": 2}
 
 
-def _config(streams=STREAMS, per_stream=PER_STREAM):
-    return {"workload": _workload(streams, per_stream), "streams": streams, "pool_N": POOL_N,
-            "passes_R": PASSES_R, "variates_per_stream_per_step": per_stream,
+def _workload(streams, per_stream, pool=POOL_N, passes=PASSES_R, dtype="f32"):
+    return (f"many_streams: {streams} streams x pool N={pool}, R={passes} passes/block, "
+            f"seeds SplitMix64(1..{streams}), {per_stream} {dtype.upper()} variates per stream per step")
+
+
+def _config(streams=STREAMS, per_stream=PER_STREAM, pool=POOL_N, passes=PASSES_R, dtype="f32"):
+    out_bytes = streams * per_stream * ESIZE[dtype]
+    return {"workload": _workload(streams, per_stream, pool, passes, dtype), "streams": streams, "pool_N": pool,
+            "passes_R": passes, "variates_per_stream_per_step": per_stream,
             "variates_per_step": streams * per_stream,
-            "output": "FP32, [stream][value] contiguous in HBM",
+            "output": f"{dtype.upper()}, [stream][value] contiguous in HBM",
             "l2": "flushed (256 MiB write) between steps, outside the per-step events; "
-                  "16 GiB of output per step also exceeds L2"}
+                  f"{out_bytes / 2**30:.3g} GiB of output per step"}
 
 
 def kernel_source_hash():
@@ -73,10 +82,10 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _algorithmic_bytes(streams, per_stream):
+def _algorithmic_bytes(streams, per_stream, pool=POOL_N, esize=4):
     """Bytes one generate launch must move: the output values plus reading and
     writing each stream's pool and header once."""
-    return streams * (per_stream * 4 + 2 * POOL_N * 4 + 2 * HDR_BYTES)
+    return streams * (per_stream * esize + 2 * pool * 4 + 2 * HDR_BYTES)
 
 
 def _traffic_per_launch(streams, per_stream):
@@ -247,7 +256,7 @@ def other_workloads(wn, torch, dev, stream, flush):
     wn.wn_set_cuda_stream(h1, stream)
     n1 = 1 << 24
     o1 = torch.empty(n1, dtype=torch.float32, device=dev)
-    shape1 = wn.wn_autotune(h1, n1, wn.WN_F32, stream)
+    shape1 = wn.wn_get_config(h1)  # the latency mode's default for one stream
     wn.wn_generate_ex(o1, n1, h1, wn.WN_F32, stream)
     t1 = _timed(torch, stream, flush, lambda: wn.wn_generate_ex(o1, n1, h1, wn.WN_F32, stream), 5)
     res["single_stream"] = {"value": n1 / (t1 / 1e3), "unit": "variates/s", "ms_per_call": t1,
@@ -262,7 +271,7 @@ def other_workloads(wn, torch, dev, stream, flush):
     prec = {}
     for dt, name, tdt in ((wn.WN_BF16, "bf16", torch.bfloat16), (wn.WN_F16, "f16", torch.float16)):
         o = o3.view(tdt)
-        shape3 = wn.wn_autotune(h3, 1 << 16, dt, stream)
+        shape3 = wn.wn_get_config_ex(h3)  # default: (16, 256, WN_CFG_IN_PLACE)
         wn.wn_generate_ex(o, per3, h3, dt, stream)
         t3 = _timed(torch, stream, flush, lambda: wn.wn_generate_ex(o, per3, h3, dt, stream), 5)
         tb = _timed(torch, stream, flush, lambda: wn.wn_boxmuller(o, per3, S3, 1, dt, stream), 5)
@@ -299,22 +308,27 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
     STREAMS, PER_STREAM = args.streams, args.per_stream
+    POOL, R, DT = args.pool, args.passes, args.dtype
+    wdt = {"f32": wn.WN_F32, "bf16": wn.WN_BF16, "f16": wn.WN_F16}[DT]
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[DT]
     seeds = rank_seeds(rank, STREAMS)
 
     t0 = time.perf_counter()
-    h = wn.wn_create_streams([POOL_N] * STREAMS, [PASSES_R] * STREAMS, seeds, WARMUP_BLOCKS, stream)
+    h = wn.wn_create_streams([POOL] * STREAMS, [R] * STREAMS, seeds, WARMUP_BLOCKS, stream)
     create_s = time.perf_counter() - t0
     if args.shape:
         qt, th = (int(v) for v in args.shape.split(","))
-        wn.wn_set_config(h, qt, th)
-        shape = wn.wn_get_config(h)
-    else:  # the library's autotuner picks the launch shape (on a copy of the state)
-        shape = wn.wn_autotune(h, min(PER_STREAM, 1 << 17), wn.WN_F32, stream)
-    out = torch.empty(STREAMS * PER_STREAM, dtype=torch.float32, device=dev)
+        wn.wn_set_config_ex(h, qt, th, wn.WN_CFG_IN_PLACE if args.in_place else 0)
+    elif args.autotune:  # the library's autotuner times the shapes on a copy of the state
+        wn.wn_autotune(h, min(PER_STREAM, 1 << 17), wdt, stream)
+    # otherwise the library's default shape for the pool size (the autotuner's
+    # pick on GB300; fixed, so that a profiler's slowdown cannot change it)
+    shape = wn.wn_get_config_ex(h)
+    out = torch.empty(STREAMS * PER_STREAM, dtype=tdt, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def step():
-        wn.wn_generate_ex(out, PER_STREAM, h, wn.WN_F32, stream)
+        wn.wn_generate_ex(out, PER_STREAM, h, wdt, stream)
 
     for _ in range(args.warmup):
         step()
@@ -341,19 +355,21 @@ def run_ours(args, rank, world, local_rank):
 
     # roofline of the generate kernel (the step is exactly one launch of it)
     peak, peak_kind = _peaks()
-    algo = _algorithmic_bytes(STREAMS, PER_STREAM)
+    algo = _algorithmic_bytes(STREAMS, PER_STREAM, POOL, ESIZE[DT])
     achieved = algo / (ms_per_step / 1e3) / 1e9
-    traffic = _traffic_per_launch(STREAMS, PER_STREAM)
+    default_kernel = (POOL, R, DT) == (POOL_N, PASSES_R, "f32")
+    traffic = _traffic_per_launch(STREAMS, PER_STREAM) if default_kernel else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "algorithmic_bytes_per_launch": algo,
-                "kernel": f"wn::generate_kernel (FP32 out, {shape[0]} quadruples x {shape[1]} compute threads "
-                          f"+ 1 control warp per stream)"}
+                "kernel": f"wn::generate_kernel ({DT.upper()} out, {shape[0]} quadruples x {shape[1]} compute "
+                          f"threads + 1 control warp per stream{', in-place pool' if shape[2] else ''})"}
     if args.kernel_only:
         wn.wn_destroy(h)
         return {"metric": METRIC, "value": value, "unit": "variates/s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_per_step, "config": _config(STREAMS, PER_STREAM),
+                "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "config": _config(STREAMS, PER_STREAM, POOL, R, DT),
                 "roofline": roofline, "gpu_launches": args.steps, "kernel_only": True}
 
     # context: a plain write of the same bytes by torch (fill_), i.e. what a
@@ -510,7 +526,15 @@ def main():
                     help="launch shape 'quadruples,threads' instead of autotuning (e.g. 8,128)")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time only the generate steps (for ncu captures of the generate kernel)")
+    ap.add_argument("--pool", type=int, default=POOL_N, help="pool size N (--kernel-only runs)")
+    ap.add_argument("--passes", type=int, default=PASSES_R, help="passes per block R (--kernel-only runs)")
+    ap.add_argument("--dtype", choices=sorted(ESIZE), default="f32", help="output type (--kernel-only runs)")
+    ap.add_argument("--in-place", action="store_true", help="with --shape: the in-place pool layout")
+    ap.add_argument("--autotune", action="store_true",
+                    help="main workload: wn_autotune's pick instead of the library default shape")
     args = ap.parse_args()
+    if (args.pool, args.passes, args.dtype) != (POOL_N, PASSES_R, "f32") and not args.kernel_only:
+        ap.error("--pool/--passes/--dtype select another workload for --kernel-only runs only")
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

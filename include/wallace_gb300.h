@@ -268,7 +268,8 @@ wn_status wn_set_config_ex(wn_stream *s, uint32_t quads_per_thread, uint32_t thr
 wn_status wn_autotune(wn_stream *s, uint64_t count, wn_dtype dtype, void *cuda_stream,
                       uint32_t *quads_per_thread, uint32_t *threads);
 
-/* wn_get_config -- the launch shape the next generate call will use. */
+/* wn_get_config -- the launch shape the next generate call will use (for a
+ * handle of few streams, the latency mode's). */
 wn_status wn_get_config(const wn_stream *s, uint32_t *quads_per_thread, uint32_t *threads);
 
 /* wn_get_config_ex -- the same and its layout flags (WN_CFG_IN_PLACE); any

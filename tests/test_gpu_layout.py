@@ -126,3 +126,12 @@ def test_in_place_rejected_where_not_compiled(wn):
         wn.wn_set_config_ex(h, 8, 128, wn.WN_CFG_IN_PLACE)  # no in-place kernel with 8 quadruples per thread
     with pytest.raises(wn.WnError):
         wn.wn_set_config_ex(h, 16, 64, 2)  # unknown flag
+
+
+def test_large_pools_default_to_in_place(wn):
+    # the library's default shape for pools of 16384 is the in-place one;
+    # pools of 4096 keep two buffers
+    h = wn.wn_create_streams([16384] * 100, [3] * 100, list(range(1, 101)))
+    assert wn.wn_get_config_ex(h) == (16, 256, wn.WN_CFG_IN_PLACE)
+    h2 = wn.wn_create_streams([4096] * 100, [2] * 100, list(range(1, 101)))
+    assert wn.wn_get_config_ex(h2) == (8, 128, 0)
