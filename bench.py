@@ -88,6 +88,23 @@ def _algorithmic_bytes(streams, per_stream, pool=POOL_N, esize=4):
     return streams * (per_stream * esize + 2 * pool * 4 + 2 * HDR_BYTES)
 
 
+def _l1_roofline(values_per_s, passes, esize, sm_mhz, sms):
+    """The shared-memory side of the kernel: L1 data-pipe wavefronts the method
+    needs per value against one 128-byte wavefront per cycle per SM.  Each
+    pass gathers one 4-byte value per lane (one wavefront per 32 values) and
+    stores four per lane as 16 bytes (one wavefront per 32 values); the output
+    stores add 32 esize bytes per 32 values (esize/4 wavefronts).  Pool loads,
+    tables and the scale are a few per block and left out."""
+    if not sm_mhz:
+        return None
+    wf = (2.0 * passes + esize / 4.0) / 32.0
+    achieved = values_per_s * wf
+    peak = sms * sm_mhz * 1e6
+    return {"bound": "l1_data_pipe", "achieved": round(achieved / 1e9, 2), "peak": round(peak / 1e9, 2),
+            "unit": "G wavefronts/s", "frac": round(achieved / peak, 4), "wavefronts_per_value": wf,
+            "peak_kind": f"{sms} SMs x 1 wavefront per cycle at the sampled {sm_mhz:.0f} MHz"}
+
+
 def _traffic_per_launch(streams, per_stream):
     """DRAM bytes per launch from the committed ncu summary (a capture with the
     same per-stream count on fewer streams, scaled by streams: every stream of
@@ -243,7 +260,7 @@ def _timed(torch, stream, flush, fn, reps):
     return t[len(t) // 2]
 
 
-def other_workloads(wn, torch, dev, stream, flush):
+def other_workloads(wn, torch, dev, stream, flush, sm_mhz=None):
     """The method's other workloads on this GPU, each timed with CUDA events:
     one stream (pool 1024, R=2, 2^24 FP32 in one call); 4096 streams of pool
     16384, R=3, 2^21 values each in BF16 and in FP16 (with Box-Muller at the
@@ -276,8 +293,9 @@ def other_workloads(wn, torch, dev, stream, flush):
         t3 = _timed(torch, stream, flush, lambda: wn.wn_generate_ex(o, per3, h3, dt, stream), 5)
         tb = _timed(torch, stream, flush, lambda: wn.wn_boxmuller(o, per3, S3, 1, dt, stream), 5)
         v = S3 * per3 / (t3 / 1e3)
+        l1 = _l1_roofline(v, R3, 2, sm_mhz, torch.cuda.get_device_properties(dev).multi_processor_count)
         prec[name] = {"value": v, "unit": "variates/s", "ms_per_step": t3, "shape": list(shape3),
-                      "hbm_frac": round(v * 2 / 1e9 / peak, 4),
+                      "hbm_frac": round(v * 2 / 1e9 / peak, 4), "l1_frac": l1["frac"] if l1 else None,
                       "boxmuller_value": S3 * per3 / (tb / 1e3), "wallace_over_boxmuller": tb / t3}
     prec["config"] = "4096 streams x pool N=16384, R=3, 2^21 values each (2^33 per type), FP32 pool, 16-bit RN output"
     res["precision"] = prec
@@ -426,7 +444,7 @@ def run_ours(args, rank, world, local_rank):
     # many-streams FP32 step above)
     configs = None
     if not args.no_configs:
-        configs = other_workloads(wn, torch, dev, stream, flush)
+        configs = other_workloads(wn, torch, dev, stream, flush, clk.summary()["sm_mhz"])
 
     # the batched uneven-request workload: 10,000 streams, pool from
     # {1024, 4096, 16384}, R from {1, 2, 4}, log-uniform lengths 2^10..2^24,
@@ -475,7 +493,10 @@ def run_ours(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": value, "unit": "variates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(STREAMS, PER_STREAM),
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+            "roofline": roofline,
+            "l1_roofline": _l1_roofline(value / world, PASSES_R, 4, clk.summary()["sm_mhz"],
+                                        torch.cuda.get_device_properties(dev).multi_processor_count),
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
             "clocks": clk.summary(),
             "comparison": {"boxmuller_philox4x32_10": {"value": bm_value, "unit": "variates/s",
                                                        "ms_per_step": bm_step,
