@@ -68,7 +68,7 @@ def test_gbm_terminal_moments_full_size(wn):
     # 2^20 paths x 252 steps, pool 4096, R = 2: E S_T = S0 e^{mu}, Var S_T =
     # S0^2 e^{2 mu}(e^{sigma^2} - 1); SE(mean) ~ 0.0207, SE(var) ~ 0.72
     import torch
-    N, R, ppg = 4096, 2, 455
+    N, R, ppg = 4096, 2, 585  # the benchmark's split
     n_paths = 1 << 20
     G = -(-n_paths // ppg)
     h = wn.wn_create_streams([N] * G, [R] * G, list(range(1, G + 1)))
