@@ -28,7 +28,10 @@
 //  * the final pass of a block scales its results in registers and stores
 //    them straight to global memory as 16-byte (FP32) or 8-byte (16-bit)
 //    aligned stores, realigned by warp shuffles (blocks of N-1 values shift
-//    the output alignment by one element per block).
+//    the output alignment by one element per block);
+//  * large pools can live in one buffer instead of two (the in-place layout:
+//    a pass gathers everything into registers before any store), so that two
+//    16384-value pools share an SM.
 // The block's scale uses the pool's sum of squares measured when the block
 // starts, which the orthogonal passes preserve exactly in exact arithmetic
 // (Section 5.5); in FP32 the two differ by the rounding of R passes.
@@ -120,8 +123,9 @@ __host__ __device__ inline size_t gen_smem_bytes(uint32_t base, uint32_t n_max, 
     return (size_t)pool_window(base, n_max, r_max) + 8 * (size_t)n_max - base;
 }
 // The in-place layout: one pool buffer right after the small part (a 16-byte
-// multiple); gather addresses are then offset + buffer (the add folds into
-// the shared load's address) instead of the OR of an aligned window.
+// multiple); gather addresses are then offset + buffer instead of the OR of
+// an aligned window (aligning one 64 KB buffer would cost a whole pool, as the
+// window's first KB is reserved).
 __host__ __device__ inline uint32_t pool_window_ip(uint32_t base, uint32_t r_max) { return base + small_bytes(r_max); }
 __host__ __device__ inline size_t gen_smem_bytes_ip(uint32_t n_max, uint32_t r_max)
 {
