@@ -125,3 +125,42 @@ def test_latency_mode_is_bit_identical_to_the_ordinary_kernel(wn, R):
         wn.wn_generate(b, count, few)
         torch.cuda.synchronize()
         assert torch.equal(a.view(n_many, count)[:3], b.view(3, count))
+
+
+def test_full_batch_recipe_sampled(wn):
+    # the batched-request workload at full size (10,000 streams, ~1.76e10 FP32
+    # values) in the launch configuration the benchmark times: wn_autotune_batch,
+    # then a captured graph, replayed once more (each stream continues); checked
+    # on sampled streams -- the longest request of each pool size, a few short
+    # and a few random ones -- against the oracle over both calls
+    import torch
+    N, R, counts = uneven_batch(10000, seed=12345)
+    seeds = np.arange(1, 10001)
+    offsets = packed_offsets(counts)
+    total = int(counts.sum())
+    h = wn.wn_create_streams(N, R, seeds)
+    out = torch.empty(total, dtype=torch.float32, device="cuda")
+    wn.wn_autotune_batch(out, counts, offsets, h)
+    rng = np.random.default_rng(3)
+    pick = set(rng.choice(10000, size=6, replace=False).tolist())
+    for n in (1024, 4096, 16384):
+        idx = np.flatnonzero(N == n)
+        pick.add(int(idx[np.argmax(counts[idx])]))
+        pick.add(int(idx[np.argmin(counts[idx])]))
+    pick = sorted(pick)
+    for call in range(2):
+        wn.wn_generate_batch(out, counts, offsets, h, use_graph=True)
+        torch.cuda.synchronize()
+        got = {i: out[int(offsets[i]): int(offsets[i] + counts[i])].cpu().numpy() for i in pick}
+        for i in pick:
+            s = oracle.Stream(int(N[i]), int(R[i]), int(seeds[i]))
+            c = int(counts[i])
+            fb = 0
+            if call:
+                s.skip(c)
+                fb = c // (int(N[i]) - 1)
+            ref = s.generate(c)
+            assert_fp32_close(got[i], ref, passes_fresh(c, int(N[i]), int(R[i]), first_block=fb) + int(R[i]),
+                              f"call {call} stream {i} N={N[i]} R={R[i]} count={c}")
+    del out
+    torch.cuda.empty_cache()
