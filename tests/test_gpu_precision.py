@@ -65,3 +65,28 @@ def test_fp32_precision_config_matches_oracle(wn, refs):
     for i, s in enumerate(STREAMS[:2]):
         rms, mx = assert_fp32_close(got[i], refs[s], passes_fresh(PER, N, R), f"N=16384 stream {s}")
         print(f"\nFP32 N=16384 R=3 stream {s}: normalised RMS error {rms:.3f}, max {mx:.2f} (units of u sqrt(P))")
+
+
+def test_full_precision_launch_sampled(wn, refs):
+    # the 16-bit workload in the launch configuration the benchmark times:
+    # 4096 streams x 2^21 BF16 values in one launch (the default in-place
+    # shape), checked on sampled streams' first 2^20 values
+    import torch
+    S, per = 4096, 1 << 21
+    h = wn.wn_create_streams([N] * S, [R] * S, list(range(1, S + 1)))
+    assert wn.wn_get_config_ex(h) == (16, 256, wn.WN_CFG_IN_PLACE)
+    out = torch.empty(S * per, dtype=torch.bfloat16, device="cuda")
+    wn.wn_generate_ex(out, per, h, 1)
+    torch.cuda.synchronize()
+    P = passes_fresh(PER, N, R)
+    for s in STREAMS:
+        got = out[(s - 1) * per:(s - 1) * per + PER].float().cpu().numpy().astype(np.float64)
+        ref = refs[s]
+        tol = U_BF16 * np.abs(ref) + 10 * U * np.sqrt(P) * (1 + np.abs(ref))
+        assert np.all(np.abs(got - ref) <= tol), (s, int(np.argmax(np.abs(got - ref) - tol)))
+    # the last value of every stream is finite and the state advanced by per
+    tail = out.view(S, per)[:, -1].float()
+    assert bool(torch.isfinite(tail).all())
+    assert wn.wn_get_state(h, S - 1)["blocks"] == 8 + -(-per // (N - 1))
+    del out
+    torch.cuda.empty_cache()
