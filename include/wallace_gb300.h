@@ -146,11 +146,13 @@ wn_status wn_generate_ex(void *out, uint64_t count, wn_stream *s, wn_dtype dtype
  * `dtype`).  If host_out is page-locked memory the device can address
  * (cudaHostAlloc, cudaHostRegister, a pinned torch tensor) and 16-byte
  * aligned, the kernel writes it directly over the host link.  Otherwise the
- * library generates in chunks into a device staging area the handle owns
- * (allocated on first use, two buffers of at most 256 MiB) and copies each
- * chunk to the host on a second CUDA stream while the next chunk is
- * generated.  Asynchronous on cuda_stream: the values are in place once
- * cuda_stream has been synchronised.
+ * values are generated into a device staging area the handle owns (allocated
+ * on first use: two buffers of 256 MiB) and copied out on a second CUDA
+ * stream while the next part is generated: a group of consecutive streams'
+ * whole requests at a time (one contiguous range of host_out per copy) when
+ * one stream's part fits 256 MiB, else every stream's next chunk per round
+ * (pitched copies).  Asynchronous on cuda_stream: the values are in place
+ * once cuda_stream has been synchronised.
  */
 wn_status wn_generate_host(void *host_out, uint64_t count, wn_stream *s, wn_dtype dtype, void *cuda_stream);
 

@@ -247,9 +247,9 @@ bool latency_default(uint32_t n_max, LaunchCfg &out)
     return false;
 }
 
-bool latency_cfg_for(const wn_stream *s, LaunchCfg &out)
+bool latency_cfg_for(const wn_stream *s, LaunchCfg &out, uint32_t n_launch)
 {
-    if (s->var || (uint32_t)s->n > (uint32_t)std::max(1, s->sms / 2)) return false;
+    if (s->var || n_launch > (uint32_t)std::max(1, s->sms / 2)) return false;
     if (s->has_cfg) {
         if (!fits_latency(s->cfg, s->n_max)) return false;
         out = s->cfg;
@@ -258,22 +258,24 @@ bool latency_cfg_for(const wn_stream *s, LaunchCfg &out)
     return latency_default(s->n_max, out);
 }
 
+// One generate launch over streams [first, first + len) of the handle (all of
+// them by default): stream first + i writes out[i count .. (i+1) count).
 wn_status launch_generate(wn_stream *s, void *out, uint64_t count, uint32_t warmup, wn_dtype dt,
-                          cudaStream_t cs)
+                          cudaStream_t cs, uint32_t first = 0, uint32_t len = 0xffffffffu)
 {
     wn::GenArgs a;
-    a.hdr = s->d_hdr;
+    a.hdr = s->d_hdr + first;
     a.pools = s->d_pools;
     a.out = out;
     a.count = count;
     a.out_stride = count;
-    a.n_streams = s->n;
+    a.n_streams = std::min(len, s->n - first);
     a.n_max = s->n_max;
     a.r_max = s->r_max;
     a.warmup_blocks = warmup;
     cudaError_t e;
     LaunchCfg lc;
-    if (warmup == 0 && count > 0 && latency_cfg_for(s, lc)) {
+    if (warmup == 0 && count > 0 && latency_cfg_for(s, lc, a.n_streams)) {
         const size_t smem = wn::gen_smem_bytes(s->smem_base, s->n_max, s->r_max);
         const bool full = s->uniform_N && (uint64_t)lc.threads * lc.qt == s->n_max / 4;
         switch (dt) {
@@ -984,7 +986,7 @@ wn_status wn_get_config_ex(const wn_stream *s, uint32_t *quads_per_thread, uint3
 {
     if (!s) return fail(WN_EINVAL, "wn_get_config: NULL handle");
     LaunchCfg c = s->has_cfg ? s->cfg : pick_cfg(s->n_max), lc;
-    if (latency_cfg_for(s, lc)) c = lc;  // few streams: the latency mode's shape
+    if (latency_cfg_for(s, lc, s->n)) c = lc;  // few streams: the latency mode's shape
     if (quads_per_thread) *quads_per_thread = (uint32_t)c.qt;
     if (threads) *threads = c.threads;
     if (flags) *flags = c.ip ? (uint32_t)WN_CFG_IN_PLACE : 0u;
@@ -1023,29 +1025,29 @@ wn_status wn_generate_host(void *host_out, uint64_t count, wn_stream *s, wn_dtyp
     if (dtype != WN_F32 && dtype != WN_BF16 && dtype != WN_F16) return fail(WN_EINVAL, "wn_generate_host: unknown dtype");
     if (count == 0) return WN_OK;
     if (!host_out) return fail(WN_EINVAL, "wn_generate_host: NULL output");
-    cudaStream_t cs0 = reinterpret_cast<cudaStream_t>(cuda_stream);
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(cuda_stream);
+    const size_t esize = dtype == WN_F32 ? 4 : 2;
+    const size_t kStageMax = size_t(256) << 20;
+    const uint64_t per_stream = count * esize;
+    // streams whose whole request fits one staging buffer (0: not even one)
+    const uint64_t group = per_stream <= kStageMax ? kStageMax / per_stream : 0;
     {
         // page-locked host memory that the device can address (every
         // cudaHostAlloc'd or registered buffer under unified addressing): the
-        // kernel stores straight into it over the host link, which on GB300
-        // beats staging plus copies for large requests (measured 182 vs 77 GB/s
-        // for 16 GiB: the pitched copies of the staged path run far below the
-        // copy engine's 193 GB/s)
+        // kernel stores straight into it over the host link -- 181 GB/s for
+        // 16 GiB on GB300, against 163 GB/s for staging groups of streams
+        // through the copy engines (which move a plain 1 GiB copy at 192 GB/s)
         cudaPointerAttributes pa{};
         if (cudaPointerGetAttributes(&pa, host_out) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
             pa.devicePointer && reinterpret_cast<uintptr_t>(pa.devicePointer) % 16 == 0) {
-            const wn_status st = launch_generate(s, pa.devicePointer, count, 0, dtype, cs0);
+            const wn_status st = launch_generate(s, pa.devicePointer, count, 0, dtype, cs);
             if (st != WN_OK) return st;
             advance_k(s, count);
             return WN_OK;
         }
         cudaGetLastError();  // an unregistered pointer is not an error here
     }
-    const size_t esize = dtype == WN_F32 ? 4 : 2;
-    const size_t kStageMax = size_t(256) << 20;
     if (!s->d_stage[0]) {
-        // per-stream chunk: a multiple of 8 values so each stream's slice of a
-        // staging buffer stays 16-byte aligned
         s->stage_bytes = kStageMax;
         for (int b = 0; b < 2; ++b) {
             WN_CU(cudaMalloc(&s->d_stage[b], s->stage_bytes));
@@ -1054,25 +1056,49 @@ wn_status wn_generate_host(void *host_out, uint64_t count, wn_stream *s, wn_dtyp
         }
         WN_CU(cudaStreamCreateWithFlags(&s->copy_cs, cudaStreamNonBlocking));
     }
-    uint64_t chunk = s->stage_bytes / (esize * (uint64_t)s->n) / 8 * 8;
-    if (chunk == 0) return fail(WN_EINVAL, "wn_generate_host: too many streams for the staging buffer");
-    if (chunk > count) chunk = count;
-    cudaStream_t cs = reinterpret_cast<cudaStream_t>(cuda_stream);
     unsigned char *dst = static_cast<unsigned char *>(host_out);
-    uint64_t done = 0;
-    for (int j = 0; done < count; ++j) {
-        const int b = j & 1;
-        const uint64_t c = std::min<uint64_t>(chunk, count - done);
-        if (j >= 2) WN_CU(cudaStreamWaitEvent(cs, s->ev_copy[b], 0));
-        wn_status st = launch_generate(s, s->d_stage[b], c, 0, dtype, cs);
-        if (st != WN_OK) return st;
-        advance_k(s, c);
-        WN_CU(cudaEventRecord(s->ev_gen[b], cs));
-        WN_CU(cudaStreamWaitEvent(s->copy_cs, s->ev_gen[b], 0));
-        WN_CU(cudaMemcpy2DAsync(dst + done * esize, count * esize, s->d_stage[b], c * esize, c * esize, s->n,
-                                cudaMemcpyDeviceToHost, s->copy_cs));
-        WN_CU(cudaEventRecord(s->ev_copy[b], s->copy_cs));
-        done += c;
+    // a previous call's copies out of the staging buffers come first
+    for (int b = 0; b < 2; ++b) WN_CU(cudaStreamWaitEvent(cs, s->ev_copy[b], 0));
+    if (group > 0) {
+        // whole requests of consecutive streams: each group's output is one
+        // contiguous range of host_out, moved by one plain copy while the
+        // next group is generated into the other staging buffer
+        int j = 0;
+        for (uint64_t g0 = 0; g0 < s->n; g0 += group, ++j) {
+            const int b = j & 1;
+            const uint32_t len = (uint32_t)std::min<uint64_t>(group, s->n - g0);
+            if (j >= 2) WN_CU(cudaStreamWaitEvent(cs, s->ev_copy[b], 0));
+            const wn_status st = launch_generate(s, s->d_stage[b], count, 0, dtype, cs, (uint32_t)g0, len);
+            if (st != WN_OK) return st;
+            WN_CU(cudaEventRecord(s->ev_gen[b], cs));
+            WN_CU(cudaStreamWaitEvent(s->copy_cs, s->ev_gen[b], 0));
+            WN_CU(cudaMemcpyAsync(dst + g0 * per_stream, s->d_stage[b], len * per_stream, cudaMemcpyDeviceToHost,
+                                  s->copy_cs));
+            WN_CU(cudaEventRecord(s->ev_copy[b], s->copy_cs));
+        }
+        advance_k(s, count);
+    } else {
+        // requests too long to stage whole: every stream's next chunk per
+        // round (a multiple of 8 values, so each stream's slice of a staging
+        // buffer stays 16-byte aligned), copied with a pitched copy
+        uint64_t chunk = s->stage_bytes / (esize * (uint64_t)s->n) / 8 * 8;
+        if (chunk == 0) return fail(WN_EINVAL, "wn_generate_host: too many streams for the staging buffer");
+        if (chunk > count) chunk = count;
+        uint64_t done = 0;
+        for (int j = 0; done < count; ++j) {
+            const int b = j & 1;
+            const uint64_t c = std::min<uint64_t>(chunk, count - done);
+            if (j >= 2) WN_CU(cudaStreamWaitEvent(cs, s->ev_copy[b], 0));
+            wn_status st = launch_generate(s, s->d_stage[b], c, 0, dtype, cs);
+            if (st != WN_OK) return st;
+            advance_k(s, c);
+            WN_CU(cudaEventRecord(s->ev_gen[b], cs));
+            WN_CU(cudaStreamWaitEvent(s->copy_cs, s->ev_gen[b], 0));
+            WN_CU(cudaMemcpy2DAsync(dst + done * esize, count * esize, s->d_stage[b], c * esize, c * esize, s->n,
+                                    cudaMemcpyDeviceToHost, s->copy_cs));
+            WN_CU(cudaEventRecord(s->ev_copy[b], s->copy_cs));
+            done += c;
+        }
     }
     // later work on cuda_stream (and its synchronisation) follows the copies
     for (int b = 0; b < 2; ++b) WN_CU(cudaStreamWaitEvent(cs, s->ev_copy[b], 0));

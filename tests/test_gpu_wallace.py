@@ -100,12 +100,16 @@ def test_continuation_is_bit_exact_and_matches_oracle(wn, torch):
 
 @pytest.mark.parametrize("pinned", [True, False])
 @pytest.mark.parametrize("Ns,Rs,half", [([1024, 4096, 64], [2, 2, 3], 50_001),
-                                         ([64] * 4096, [2] * 4096, 20_000)])
+                                         ([64] * 4096, [2] * 4096, 20_000),
+                                         ([1024] * 64, [2] * 64, 1 << 21),
+                                         ([4096, 1024], [2, 1], (1 << 26) + 8)])
 def test_generate_host_equals_device_path(wn, torch, Ns, Rs, half, pinned):
-    # pinned host memory: the kernel writes it directly; pageable memory: the
-    # values travel through staging buffers -- in the second case
-    # 4096 x 20000 x 4 B > 256 MiB per call, so in several chunks with
-    # overlapped copies
+    # every route to host memory gives the device path's values: pinned
+    # memory is written by the kernel directly; pageable memory is staged --
+    # 4096 x 20000 x 4 B (> 256 MiB) in two groups of consecutive streams,
+    # 64 x 2^21 x 4 B in groups of 32 streams, and 2 x (2^26 + 8) x 4 B (each
+    # stream's part above 256 MiB) in rounds of per-stream chunks with pitched
+    # copies
     n = len(Ns)
     seeds = list(range(5, 5 + n))
     dev = _gen(wn, torch, wn.wn_create_streams(Ns, Rs, seeds), 2 * half).cpu().view(n, 2 * half)
