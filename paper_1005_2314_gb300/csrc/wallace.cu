@@ -352,8 +352,8 @@ LaunchCfg latency_cfg(uint32_t N)
 // about 400 + N/20 ns against 0.34 ps per value-pass over the machine --
 // would set the batch's length; up to a third of the SMs' worth of such
 // requests (longest first) get exclusive groups instead: one CTA per SM with
-// the lowest-latency shape, so that no other CTA shares their SM.  After
-// wn_autotune_batch, `crit` (s->batch_crit) fixes how many of the longest
+// the lowest-latency shape, so that no other CTA shares their SM.  crit_k >= 0
+// (after wn_autotune_batch: s->batch_crit) fixes how many of the longest
 // chains get them instead of the estimate's threshold.
 std::vector<Group> plan_batch(const wn_stream *s, const uint64_t *counts, std::vector<uint32_t> &order, int crit_k)
 {
