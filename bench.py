@@ -43,7 +43,7 @@ METRIC = "N(0,1) variates/s on 1 GB300, % of HBM-write roofline, vs Box–Muller
 STREAMS, POOL_N, PASSES_R, PER_STREAM = 4096, 4096, 2, 1 << 20
 WARMUP_BLOCKS = 8
 HDR_BYTES = 96
-KERNEL_SOURCES = ("wn_gen.cuh", "wn_device.cuh")
+KERNEL_SOURCES = ("wn_group.cuh", "wn_gen.cuh", "wn_device.cuh")
 
 
 ESIZE = {"f32": 4, "bf16": 2, "f16": 2}
@@ -288,7 +288,7 @@ def other_workloads(wn, torch, dev, stream, flush, sm_mhz=None):
     prec = {}
     for dt, name, tdt in ((wn.WN_BF16, "bf16", torch.bfloat16), (wn.WN_F16, "f16", torch.float16)):
         o = o3.view(tdt)
-        shape3 = wn.wn_get_config_ex(h3)  # default: (16, 256, WN_CFG_IN_PLACE)
+        shape3 = wn.wn_get_config_ex(h3)  # default: group mode, 4 warps x 32 quadruples per lane
         wn.wn_generate_ex(o, per3, h3, dt, stream)
         t3 = _timed(torch, stream, flush, lambda: wn.wn_generate_ex(o, per3, h3, dt, stream), 5)
         tb = _timed(torch, stream, flush, lambda: wn.wn_boxmuller(o, per3, S3, 1, dt, stream), 5)
@@ -339,7 +339,8 @@ def run_ours(args, rank, world, local_rank):
     create_s = time.perf_counter() - t0
     if args.shape:
         qt, th = (int(v) for v in args.shape.split(","))
-        wn.wn_set_config_ex(h, qt, th, wn.WN_CFG_IN_PLACE if args.in_place else 0)
+        wn.wn_set_config_ex(h, qt, th, (wn.WN_CFG_IN_PLACE if args.in_place else 0) |
+                            (wn.WN_CFG_GROUP if args.group else 0))
     elif args.autotune:  # the library's autotuner times the shapes on a copy of the state
         wn.wn_autotune(h, min(PER_STREAM, 1 << 17), wdt, stream)
     # otherwise the library's default shape for the pool size (the autotuner's
@@ -384,8 +385,10 @@ def run_ours(args, rank, world, local_rank):
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "algorithmic_bytes_per_launch": algo,
-                "kernel": f"wn::generate_kernel ({DT.upper()} out, {shape[0]} quadruples x {shape[1]} compute "
-                          f"threads + 1 control warp per stream{', in-place pool' if shape[2] else ''})"}
+                "kernel": (f"wn::group_kernel ({DT.upper()} out, {shape[1] // 32} warps x {shape[0]} quadruples "
+                           f"per lane per stream, no control warp, in-place pool)" if shape[2] & 2 else
+                           f"wn::generate_kernel ({DT.upper()} out, {shape[0]} quadruples x {shape[1]} compute "
+                           f"threads + 1 control warp per stream{', in-place pool' if shape[2] else ''})")}
     if args.kernel_only:
         wn.wn_destroy(h)
         return {"metric": METRIC, "value": value, "unit": "variates/s", "n_gpus": world, "steps": args.steps,
@@ -554,6 +557,8 @@ def main():
     ap.add_argument("--passes", type=int, default=PASSES_R, help="passes per block R (--kernel-only runs)")
     ap.add_argument("--dtype", choices=sorted(ESIZE), default="f32", help="output type (--kernel-only runs)")
     ap.add_argument("--in-place", action="store_true", help="with --shape: the in-place pool layout")
+    ap.add_argument("--group", action="store_true",
+                    help="with --shape 'quadruples per lane,threads': the group-mode kernel")
     ap.add_argument("--autotune", action="store_true",
                     help="main workload: wn_autotune's pick instead of the library default shape")
     args = ap.parse_args()

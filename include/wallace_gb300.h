@@ -148,11 +148,13 @@ wn_status wn_generate_ex(void *out, uint64_t count, wn_stream *s, wn_dtype dtype
  * aligned, the kernel writes it directly over the host link.  Otherwise the
  * values are generated into a device staging area the handle owns (allocated
  * on first use: two buffers of 256 MiB) and copied out on a second CUDA
- * stream while the next part is generated: a group of consecutive streams'
- * whole requests at a time (one contiguous range of host_out per copy) when
- * one stream's part fits 256 MiB, else every stream's next chunk per round
- * (pitched copies).  Asynchronous on cuda_stream: the values are in place
- * once cuda_stream has been synchronised.
+ * stream: a group of consecutive streams' whole requests at a time (one
+ * contiguous range of host_out per copy) when one stream's part fits 256 MiB,
+ * else every stream's next chunk per round (pitched copies).  A copy into
+ * pageable memory returns to the host only when it is done, so on that route
+ * the call returns after its copies and generation and copies take turns.
+ * On the page-locked route the call is asynchronous on cuda_stream: the
+ * values are in place once cuda_stream has been synchronised.
  */
 wn_status wn_generate_host(void *host_out, uint64_t count, wn_stream *s, wn_dtype dtype, void *cuda_stream);
 
@@ -167,8 +169,15 @@ wn_status wn_generate_host(void *host_out, uint64_t count, wn_stream *s, wn_dtyp
  * use_graph != 0: the counter reset and the group launches are captured once
  * into a CUDA graph kept by the handle, and later calls with the same out,
  * counts, offsets and dtype replay it (a call with other arguments captures
- * anew).  Streams continue their sequences as with wn_generate.
- * Asynchronous on cuda_stream.
+ * anew).  The graph reads a device copy of the descriptors of its own, which
+ * calls with use_graph = 0 and wn_autotune_batch never touch, so eager calls
+ * may come between replays.  Streams continue their sequences as with
+ * wn_generate.  counts and offsets are copied (through a host buffer of the
+ * library's) before the call returns: the caller may reuse or free them at
+ * once, page-locked or not.  Asynchronous on cuda_stream; an upload of new
+ * descriptors waits for the work already enqueued on cuda_stream.  Successive
+ * calls on one handle must be ordered on the GPU (one CUDA stream, or
+ * synchronisation between them).
  */
 wn_status wn_generate_batch(void *out, const uint64_t *counts, const uint64_t *offsets, wn_stream *s,
                             wn_dtype dtype, int use_graph, void *cuda_stream);
@@ -184,14 +193,16 @@ wn_status wn_generate_batch(void *out, const uint64_t *counts, const uint64_t *o
  * counters and the request descriptors live in one fixed array of device
  * memory compiled into the library (about 320 KB, resident on every device
  * that loads the library until the process exits), so it serves at most
- * WN_NOALLOC_MAX_STREAMS streams (WN_EINVAL beyond, or with more pool sizes
- * than the array's 16 counters).  The groups run one after another on
+ * WN_NOALLOC_MAX_STREAMS streams (WN_EINVAL beyond; the 13 possible pool
+ * sizes always fit its 16 counters).  The groups run one after another on
  * cuda_stream.  The first call on a device looks up the array's device
- * address there (with that device current); make that first call before any
- * stream capture.  Every call shares the array: calls whose work overlaps on
- * the GPU (e.g. on two CUDA streams at once) race on it, so order them on one
- * stream or synchronise in between.  The handle's device must be current.
- * The paper has no counterpart to this entry point.
+ * address there (with that device current).  The call copies the caller's
+ * counts and offsets and advances the streams' positions on the host when it
+ * is made, so it must not be recorded into a CUDA graph: WN_EINVAL while
+ * cuda_stream is being captured.  Every call shares the array: calls whose
+ * work overlaps on the GPU (e.g. on two CUDA streams at once) race on it, so
+ * order them on one stream or synchronise in between.  The handle's device
+ * must be current.  The paper has no counterpart to this entry point.
  */
 #define WN_NOALLOC_MAX_STREAMS 16384u
 wn_status wn_generate_batch_noalloc(void *out, const uint64_t *counts, const uint64_t *offsets, wn_stream *s,
@@ -255,6 +266,23 @@ wn_status wn_set_config(wn_stream *s, uint32_t quads_per_thread, uint32_t thread
  * streams that would take the latency mode use the ordinary kernel instead.
  */
 #define WN_CFG_IN_PLACE 1u
+/*
+ * WN_CFG_GROUP selects the group-mode kernel for handles of the plain method
+ * whose streams share one pool size: threads / 32 warps own each stream with
+ * no control warp (each warp draws and derives every pass's permutation and
+ * signs itself, Sections 5.2, 5.4 and 5.8), the pool stays in one
+ * shared-memory buffer, and each block's scale (Section 5.5) is formed at the
+ * end of the block before it.  quads_per_thread is then the quadruples per
+ * lane, with 128 * quads_per_thread * (threads / 32) = pool_N; compiled for
+ * (pool 1024: 8, 32), (2048: 16, 32), (4096: 32, 32), (4096: 16, 64),
+ * (8192: 32, 64), (16384: 32, 128).  The launch pads each CTA's shared memory
+ * so that the streams fill whole waves of the SMs.  Values agree with the
+ * ordinary kernel's within the FP32 tolerance (the sums of squares are added
+ * in another order); integer streams are identical.  WN_EINVAL for other
+ * shapes, variants, mixed pool sizes, or a device whose dynamic shared memory
+ * does not start at window address 1024.
+ */
+#define WN_CFG_GROUP 2u
 wn_status wn_set_config_ex(wn_stream *s, uint32_t quads_per_thread, uint32_t threads, uint32_t flags);
 
 /*
@@ -274,7 +302,8 @@ wn_status wn_autotune(wn_stream *s, uint64_t count, wn_dtype dtype, void *cuda_s
  * handle of few streams, the latency mode's). */
 wn_status wn_get_config(const wn_stream *s, uint32_t *quads_per_thread, uint32_t *threads);
 
-/* wn_get_config_ex -- the same and its layout flags (WN_CFG_IN_PLACE); any
+/* wn_get_config_ex -- the same and its layout flags (WN_CFG_IN_PLACE,
+ * WN_CFG_GROUP); any
  * output pointer may be NULL. */
 wn_status wn_get_config_ex(const wn_stream *s, uint32_t *quads_per_thread, uint32_t *threads, uint32_t *flags);
 
@@ -302,8 +331,9 @@ wn_status wn_get_state(const wn_stream *s, uint32_t i, uint64_t *host_xw, double
  * wn_save -- checkpoint: serialise the complete state of every stream of the
  * handle (generator words, Section 5.8; pool, reserved value, sum of squares,
  * block count and the position within the last block, Section 5.5) into the
- * caller's host buffer.  Synchronises the handle's CUDA stream first, so the
- * state includes every call enqueued before.  With host_buf == NULL only
+ * caller's host buffer.  Synchronises the handle's device first, so the state
+ * includes every call enqueued before on any CUDA stream (the caller's
+ * current device is left as it was).  With host_buf == NULL only
  * *bytes_needed is set.  Layout (little-endian, version 1): 8-byte magic
  * "WNSTATE1", uint32 stream count, uint32 header size (96), the 96-byte
  * per-stream headers, the pools as FP32 in stream order, and an FNV-1a 64

@@ -14,6 +14,7 @@
 
 #include "wallace_gb300.h"
 #include "wn_gen.cuh"
+#include "wn_group.cuh"
 
 namespace wn {
 
@@ -100,6 +101,16 @@ __global__ void draws_kernel(uint64_t seed, uint64_t n, uint64_t *out)
 // ===========================================================================
 
 
+// Device copy of a batch's request descriptors, in one allocation: output
+// offsets and counts (uint64 per stream), the claim order (uint32 per
+// stream; each pool-size group's streams, longest first) and 16 claim
+// counters (one per group).
+struct BatchDesc {
+    unsigned char *base = nullptr;
+    uint64_t *counts = nullptr, *offsets = nullptr;
+    uint32_t *order = nullptr, *queue = nullptr;
+};
+
 struct wn_stream {
     int device = 0;
     uint32_t n = 0;
@@ -123,9 +134,11 @@ struct wn_stream {
     int smem_optin = 0;  // largest dynamic shared memory a CTA may request
     // batches (wn_generate_batch): per-stream descriptors on the device, one
     // claim counter per pool-size group, branch streams for the groups, the
-    // tuned shape per pool size, and the last captured graph
-    uint64_t *d_bcounts = nullptr, *d_boffsets = nullptr;
-    uint32_t *d_border = nullptr, *d_queue = nullptr;
+    // tuned shape per pool size, and the last captured graph.  The graph reads
+    // descriptors of its own (bd_graph), which only a new capture rewrites, so
+    // that eager calls and the tuner (bd_eager) never change what a cached
+    // graph replays.
+    BatchDesc bd_eager, bd_graph;
     std::vector<cudaStream_t> branch;
     std::vector<cudaEvent_t> join;
     // branch streams of the greatest priority, for exclusive groups: their
@@ -152,6 +165,8 @@ struct wn_stream {
     // launch configuration chosen by wn_set_config (otherwise the default)
     bool has_cfg = false;
     wn::LaunchCfg cfg{};
+    // CTAs per SM the last group-mode launch was sized for
+    uint32_t group_ctas = 0;
 };
 
 namespace {
@@ -211,6 +226,57 @@ LaunchCfg pick_cfg(uint32_t n_max)
     if (nq <= 1024) return {8, 160, nq / 8};
     if (nq >= 4096) return {16, 288, nq / 16, 1};
     return {8, 544, nq / 8};
+}
+
+// A compiled group-mode shape (wn::kGroupShapes) for pool N with G warps.
+bool group_shape_ok(uint32_t N, uint32_t G)
+{
+    for (const auto &k : wn::kGroupShapes)
+        if ((uint32_t)k[0] == N && (uint32_t)k[1] == G) return true;
+    return false;
+}
+
+// Group mode serves handles of the plain method whose streams all have one
+// pool size, when dynamic shared memory starts where the kernel expects it.
+bool group_eligible(const wn_stream *s)
+{
+    return !s->var && s->uniform_N && s->smem_base == wn::kGroupBase;
+}
+
+// The group-mode shape of pool N with G warps per stream.
+LaunchCfg group_cfg_of(uint32_t N, uint32_t G)
+{
+    LaunchCfg c{(int)(N / (128u * G)), (int)(32u * G), 32u * G, 1};
+    c.grp = 1;
+    return c;
+}
+
+// Pool sizes whose default launch is the group mode, with its warps per
+// stream (other sizes keep pick_cfg's shapes).  Measured on GB300 against
+// the ordinary kernel's defaults: 4096 streams of pool 4096, R = 2, 2^20 FP32
+// each, 3.18 ms (one warp per stream) against 3.65; 4864 streams of pool
+// 1024, 11.5 -> 3.8 ms; 4096 streams of pool 16384, R = 3, 2^21 BF16 each,
+// 10.6 -> 8.3 ms (four warps per stream); two warps per stream of pool 4096
+// were slower than one (1.31e12 against 1.36e12 values/s at equal waves).
+bool group_default(uint32_t N, uint32_t &G)
+{
+    switch (N) {
+    case 1024:
+    case 2048:
+    case 4096: G = 1; return true;
+    case 8192: G = 2; return true;
+    case 16384: G = 4; return true;
+    default: G = 0; return false;
+    }
+}
+
+// The launch shape a generate call of the handle uses when none was set.
+LaunchCfg default_cfg(const wn_stream *s)
+{
+    uint32_t G = 0;
+    if (group_eligible(s) && group_default(s->n_max, G) && group_shape_ok(s->n_max, G))
+        return group_cfg_of(s->n_max, G);
+    return pick_cfg(s->n_max);
 }
 
 // The latency mode (two control warps beside the compute warps; see
@@ -287,7 +353,19 @@ wn_status launch_generate(wn_stream *s, void *out, uint64_t count, uint32_t warm
         if (e != cudaSuccess) return cuda_fail("generate launch (latency mode)", e);
         return WN_OK;
     }
-    const LaunchCfg c = s->has_cfg ? s->cfg : pick_cfg(s->n_max);
+    LaunchCfg c = s->has_cfg ? s->cfg : default_cfg(s);
+    if (c.grp && warmup == 0 && group_eligible(s)) {
+        const uint32_t G = c.threads / 32u;
+        switch (dt) {
+        case WN_F32: e = wn::launch_group_f32(a, s->n_max, G, s->sms, cs, &s->group_ctas); break;
+        case WN_BF16: e = wn::launch_group_bf16(a, s->n_max, G, s->sms, cs, &s->group_ctas); break;
+        case WN_F16: e = wn::launch_group_f16(a, s->n_max, G, s->sms, cs, &s->group_ctas); break;
+        default: return fail(WN_EINVAL, "unknown dtype");
+        }
+        if (e != cudaSuccess) return cuda_fail("generate launch (group mode)", e);
+        return WN_OK;
+    }
+    if (c.grp) c = pick_cfg(s->n_max);  // warm-up blocks run in the ordinary kernel
     const size_t smem = cfg_smem(s, c, s->n_max, s->r_max);
     // every stream's quadruples exactly fill the CTA: no per-quadruple checks
     const bool full = s->uniform_N && (uint64_t)c.threads * c.qt == s->n_max / 4;
@@ -410,15 +488,43 @@ std::vector<Group> plan_batch(const wn_stream *s, const uint64_t *counts, std::v
     return groups;
 }
 
+// Byte layout of a BatchDesc for n streams: counts, offsets, order, counters.
+constexpr size_t desc_counters(size_t n) { return (20 * n + 15) / 16 * 16; }
+
+wn_status alloc_desc(wn_stream *s, BatchDesc &d)
+{
+    if (d.base) return WN_OK;
+    const size_t n = s->n;
+    WN_CU(cudaMalloc(&d.base, desc_counters(n) + 16 * sizeof(uint32_t)));
+    d.counts = reinterpret_cast<uint64_t *>(d.base);
+    d.offsets = reinterpret_cast<uint64_t *>(d.base + 8 * n);
+    d.order = reinterpret_cast<uint32_t *>(d.base + 16 * n);
+    d.queue = reinterpret_cast<uint32_t *>(d.base + desc_counters(n));
+    return WN_OK;
+}
+
+// Uploads counts, offsets and the claim order into d with one copy from a
+// pageable host buffer of the library's own: a copy from pageable memory has
+// consumed its source when it returns, so the caller may reuse or free its
+// arrays as soon as the call returns, whether they are page-locked or not.
+wn_status upload_desc(wn_stream *s, const BatchDesc &d, const uint64_t *counts, const uint64_t *offsets,
+                      const std::vector<uint32_t> &order, cudaStream_t cs)
+{
+    const size_t n = s->n;
+    std::vector<unsigned char> host(20 * n);
+    std::memcpy(host.data(), counts, 8 * n);
+    std::memcpy(host.data() + 8 * n, offsets, 8 * n);
+    std::memcpy(host.data() + 16 * n, order.data(), 4 * n);
+    WN_CU(cudaMemcpyAsync(d.base, host.data(), host.size(), cudaMemcpyHostToDevice, cs));
+    return WN_OK;
+}
+
 wn_status ensure_batch_buffers(wn_stream *s, size_t n_groups)
 {
-    if (!s->d_bcounts) {
-        WN_CU(cudaMalloc(&s->d_bcounts, sizeof(uint64_t) * s->n));
-        WN_CU(cudaMalloc(&s->d_boffsets, sizeof(uint64_t) * s->n));
-        WN_CU(cudaMalloc(&s->d_border, sizeof(uint32_t) * s->n));
-        WN_CU(cudaMalloc(&s->d_queue, sizeof(uint32_t) * 16));
-        WN_CU(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming));
-    }
+    wn_status st = alloc_desc(s, s->bd_eager);
+    if (st == WN_OK) st = alloc_desc(s, s->bd_graph);
+    if (st != WN_OK) return st;
+    if (!s->fork) WN_CU(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming));
     while (s->branch.size() < n_groups) {
         cudaStream_t b, bh;
         cudaEvent_t j;
@@ -440,12 +546,13 @@ LaunchCfg group_cfg(const wn_stream *s, uint32_t N)
     return it != s->group_cfg.end() ? it->second : pick_cfg(N);
 }
 
-// Enqueues a batch whose descriptors are already on the device: reset the
-// claim counters, fork one branch per group, launch each group's persistent
-// kernel, join.
-wn_status enqueue_batch(wn_stream *s, const std::vector<Group> &groups, void *out, wn_dtype dt, cudaStream_t cs)
+// Enqueues a batch whose descriptors are already on the device (in d): reset
+// the claim counters, fork one branch per group, launch each group's
+// persistent kernel, join.
+wn_status enqueue_batch(wn_stream *s, const std::vector<Group> &groups, void *out, wn_dtype dt, cudaStream_t cs,
+                        const BatchDesc &d)
 {
-    WN_CU(cudaMemsetAsync(s->d_queue, 0, sizeof(uint32_t) * 16, cs));
+    WN_CU(cudaMemsetAsync(d.queue, 0, sizeof(uint32_t) * 16, cs));
     WN_CU(cudaEventRecord(s->fork, cs));
     for (size_t gi = 0; gi < groups.size(); ++gi) {
         const Group &g = groups[gi];
@@ -462,11 +569,11 @@ wn_status enqueue_batch(wn_stream *s, const std::vector<Group> &groups, void *ou
         a.r_max = g.r_max;
         a.warmup_blocks = 0;
         wn::BatchArgs bq;
-        bq.order = s->d_border + g.start;
-        bq.offsets = s->d_boffsets;
-        bq.counts = s->d_bcounts;
+        bq.order = d.order + g.start;
+        bq.offsets = d.offsets;
+        bq.counts = d.counts;
         bq.n_items = g.len;
-        bq.queue = s->d_queue + gi;
+        bq.queue = d.queue + gi;
         size_t smem = wn::gen_smem_bytes(s->smem_base, g.N, g.r_max);
         if (g.exclusive) smem = std::max(smem, (size_t)s->smem_optin);  // nothing else fits on its SM
         cudaError_t e;
@@ -713,10 +820,16 @@ wn_status wn_save(const wn_stream *s, void *host_buf, uint64_t buf_bytes, uint64
     const uint32_t n = s->n, hb = (uint32_t)sizeof(wn::StreamHdr);
     std::memcpy(b + 8, &n, 4);
     std::memcpy(b + 12, &hb, 4);
-    cudaError_t e = cudaStreamSynchronize(s->cs);
+    // every call enqueued before, on whichever CUDA stream (calls take their
+    // own streams, and wn_generate_host copies on a second one), has finished
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e == cudaSuccess && cur != s->device) e = cudaSetDevice(s->device);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMemcpy(b + 16, s->d_hdr, (size_t)hb * n, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess)
         e = cudaMemcpy(b + 16 + (size_t)hb * n, s->d_pools, 4 * pool_elems, cudaMemcpyDeviceToHost);
+    if (cur >= 0 && cur != s->device) cudaSetDevice(cur);  // the caller's device stays current
     if (e != cudaSuccess) return cuda_fail("wn_save: copy", e);
     wn::StreamHdr *h = reinterpret_cast<wn::StreamHdr *>(b + 16);
     for (uint32_t i = 0; i < n; ++i) {
@@ -827,10 +940,8 @@ void wn_destroy(wn_stream *s)
         if (s->ev_copy[b]) cudaEventDestroy(s->ev_copy[b]);
     }
     if (s->copy_cs) cudaStreamDestroy(s->copy_cs);
-    if (s->d_bcounts) cudaFree(s->d_bcounts);
-    if (s->d_boffsets) cudaFree(s->d_boffsets);
-    if (s->d_border) cudaFree(s->d_border);
-    if (s->d_queue) cudaFree(s->d_queue);
+    if (s->bd_eager.base) cudaFree(s->bd_eager.base);
+    if (s->bd_graph.base) cudaFree(s->bd_graph.base);
     for (auto b : s->branch) cudaStreamDestroy(b);
     for (auto b : s->branch_hi) cudaStreamDestroy(b);
     for (auto j : s->join) cudaEventDestroy(j);
@@ -842,9 +953,23 @@ void wn_destroy(wn_stream *s)
 wn_status wn_set_config_ex(wn_stream *s, uint32_t quads_per_thread, uint32_t threads, uint32_t flags)
 {
     if (!s) return fail(WN_EINVAL, "wn_set_config: NULL handle");
-    if (flags & ~(uint32_t)WN_CFG_IN_PLACE) return fail(WN_EINVAL, "wn_set_config_ex: unknown flags");
+    if (flags & ~(uint32_t)(WN_CFG_IN_PLACE | WN_CFG_GROUP)) return fail(WN_EINVAL, "wn_set_config_ex: unknown flags");
     if (quads_per_thread == 0 && threads == 0) {
         s->has_cfg = false;
+        return WN_OK;
+    }
+    if (flags & WN_CFG_GROUP) {
+        const uint32_t G = threads / 32u;
+        if (threads % 32u != 0 || G == 0 || !group_shape_ok(s->n_max, G) ||
+            (uint64_t)128u * quads_per_thread * G != s->n_max)
+            return fail(WN_EINVAL, "wn_set_config_ex: no compiled group-mode shape with " +
+                                       std::to_string(quads_per_thread) + " quadruples per lane and " +
+                                       std::to_string(threads) + " threads covers pool " + std::to_string(s->n_max));
+        if (!group_eligible(s))
+            return fail(WN_EINVAL, "wn_set_config_ex: group mode needs one pool size, the plain method and "
+                                   "dynamic shared memory at its expected window address");
+        s->cfg = group_cfg_of(s->n_max, G);
+        s->has_cfg = true;
         return WN_OK;
     }
     // the instantiation of the asked layout with the smallest thread bound
@@ -906,6 +1031,9 @@ wn_status wn_autotune(wn_stream *s, uint64_t count, wn_dtype dtype, void *cuda_s
                 if (!dup) cand.push_back(c);
             }
         }
+    if (group_eligible(s))  // the compiled group-mode shapes of this pool size
+        for (const auto &k : wn::kGroupShapes)
+            if ((uint32_t)k[0] == s->n_max) cand.push_back(group_cfg_of(s->n_max, (uint32_t)k[1]));
     if (cand.empty()) return fail(WN_EINVAL, "wn_autotune: no compiled shape fits");
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(cuda_stream);
     const size_t esize = dtype == WN_F32 ? 4 : 2;
@@ -985,11 +1113,11 @@ wn_status wn_autotune(wn_stream *s, uint64_t count, wn_dtype dtype, void *cuda_s
 wn_status wn_get_config_ex(const wn_stream *s, uint32_t *quads_per_thread, uint32_t *threads, uint32_t *flags)
 {
     if (!s) return fail(WN_EINVAL, "wn_get_config: NULL handle");
-    LaunchCfg c = s->has_cfg ? s->cfg : pick_cfg(s->n_max), lc;
+    LaunchCfg c = s->has_cfg ? s->cfg : default_cfg(s), lc;
     if (latency_cfg_for(s, lc, s->n)) c = lc;  // few streams: the latency mode's shape
     if (quads_per_thread) *quads_per_thread = (uint32_t)c.qt;
     if (threads) *threads = c.threads;
-    if (flags) *flags = c.ip ? (uint32_t)WN_CFG_IN_PLACE : 0u;
+    if (flags) *flags = (c.ip ? (uint32_t)WN_CFG_IN_PLACE : 0u) | (c.grp ? (uint32_t)WN_CFG_GROUP : 0u);
     return WN_OK;
 }
 
@@ -1061,8 +1189,10 @@ wn_status wn_generate_host(void *host_out, uint64_t count, wn_stream *s, wn_dtyp
     for (int b = 0; b < 2; ++b) WN_CU(cudaStreamWaitEvent(cs, s->ev_copy[b], 0));
     if (group > 0) {
         // whole requests of consecutive streams: each group's output is one
-        // contiguous range of host_out, moved by one plain copy while the
-        // next group is generated into the other staging buffer
+        // contiguous range of host_out, moved by one plain copy.  A copy into
+        // pageable memory returns only once it is done, so the next group's
+        // kernel is enqueued after it: generation and copies alternate (the
+        // copies, not the kernels, set the pace)
         int j = 0;
         for (uint64_t g0 = 0; g0 < s->n; g0 += group, ++j) {
             const int b = j & 1;
@@ -1080,7 +1210,8 @@ wn_status wn_generate_host(void *host_out, uint64_t count, wn_stream *s, wn_dtyp
     } else {
         // requests too long to stage whole: every stream's next chunk per
         // round (a multiple of 8 values, so each stream's slice of a staging
-        // buffer stays 16-byte aligned), copied with a pitched copy
+        // buffer stays 16-byte aligned), copied with a pitched copy (which,
+        // into pageable memory, also returns once it is done)
         uint64_t chunk = s->stage_bytes / (esize * (uint64_t)s->n) / 8 * 8;
         if (chunk == 0) return fail(WN_EINVAL, "wn_generate_host: too many streams for the staging buffer");
         if (chunk > count) chunk = count;
@@ -1118,27 +1249,25 @@ wn_status wn_generate_batch(void *out, const uint64_t *counts, const uint64_t *o
     const bool same = use_graph && s->gexec && s->g_out == out && s->g_dtype == (int)dtype &&
                       std::equal(counts, counts + s->n, s->g_counts.begin()) &&
                       std::equal(offsets, offsets + s->n, s->g_offsets.begin());
-    if (!same) {
-        WN_CU(cudaMemcpyAsync(s->d_bcounts, counts, sizeof(uint64_t) * s->n, cudaMemcpyHostToDevice, cs));
-        WN_CU(cudaMemcpyAsync(s->d_boffsets, offsets, sizeof(uint64_t) * s->n, cudaMemcpyHostToDevice, cs));
-        WN_CU(cudaMemcpyAsync(s->d_border, order.data(), sizeof(uint32_t) * s->n, cudaMemcpyHostToDevice, cs));
-    }
     if (!use_graph) {
-        if ((st = enqueue_batch(s, groups, out, dtype, cs)) != WN_OK) return st;
+        if ((st = upload_desc(s, s->bd_eager, counts, offsets, order, cs)) != WN_OK) return st;
+        if ((st = enqueue_batch(s, groups, out, dtype, cs, s->bd_eager)) != WN_OK) return st;
     } else {
         if (!same) {
-            // capture the counters' reset and the groups' launches once; the
-            // descriptors they read were uploaded above, in stream order
+            // the graph's own descriptors, then one capture of the counters'
+            // reset and the groups' launches reading them (the upload is in
+            // stream order before the graph's first launch)
             if (s->gexec) {
                 cudaGraphExecDestroy(s->gexec);
                 s->gexec = nullptr;
             }
+            if ((st = upload_desc(s, s->bd_graph, counts, offsets, order, cs)) != WN_OK) return st;
             cudaStream_t cap = nullptr;
             WN_CU(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
             cudaGraph_t graph = nullptr;
             cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                st = enqueue_batch(s, groups, out, dtype, cap);
+                st = enqueue_batch(s, groups, out, dtype, cap, s->bd_graph);
                 e = cudaStreamEndCapture(cap, &graph);
             }
             // keep the captured streams' priorities (exclusive groups first)
@@ -1169,9 +1298,8 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
     const std::vector<Group> groups = plan_batch(s, counts, order, -1);
     if (groups.size() > 16) return fail(WN_EINVAL, "wn_autotune_batch: more than 16 pool sizes");
     if ((st = ensure_batch_buffers(s, groups.size())) != WN_OK) return st;
-    WN_CU(cudaMemcpyAsync(s->d_bcounts, counts, sizeof(uint64_t) * s->n, cudaMemcpyHostToDevice, cs));
-    WN_CU(cudaMemcpyAsync(s->d_boffsets, offsets, sizeof(uint64_t) * s->n, cudaMemcpyHostToDevice, cs));
-    WN_CU(cudaMemcpyAsync(s->d_border, order.data(), sizeof(uint32_t) * s->n, cudaMemcpyHostToDevice, cs));
+    const BatchDesc &d = s->bd_eager;
+    if ((st = upload_desc(s, d, counts, offsets, order, cs)) != WN_OK) return st;
     size_t pool_floats = 0;
     for (uint32_t i = 0; i < s->n; ++i) pool_floats += s->N[i];
     wn::StreamHdr *hdr_bak = nullptr;
@@ -1189,6 +1317,9 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
             r = cudaMemcpyAsync(s->d_pools, pool_bak, sizeof(float) * pool_floats, cudaMemcpyDeviceToDevice, cs);
         return r;
     };
+    // the trials below set the handle's shapes; an error restores these
+    const std::map<uint32_t, LaunchCfg> old_cfg = s->group_cfg;
+    const std::map<uint32_t, bool> old_lat = s->group_lat;
     std::map<uint32_t, LaunchCfg> chosen;
     std::map<uint32_t, bool> chosen_lat;
     for (size_t gi = 0; gi < groups.size() && e == cudaSuccess; ++gi) {
@@ -1206,13 +1337,13 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
                 float times[2] = {0.f, 0.f};
                 for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
                     e = restore();
-                    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_queue, 0, sizeof(uint32_t) * 16, cs);
+                    if (e == cudaSuccess) e = cudaMemsetAsync(d.queue, 0, sizeof(uint32_t) * 16, cs);
                     if (e == cudaSuccess) e = cudaEventRecord(e0, cs);
                     if (e == cudaSuccess) {
                         const bool full = true;
                         const size_t smem = cfg_smem(s, c, g.N, g.r_max);
                         wn::GenArgs a{s->d_hdr, s->d_pools, out, 0, 0, g.len, g.N, g.r_max, 0};
-                        wn::BatchArgs bq{s->d_border + g.start, s->d_boffsets, s->d_bcounts, g.len, s->d_queue};
+                        wn::BatchArgs bq{d.order + g.start, d.offsets, d.counts, g.len, d.queue};
                         switch (dtype) {
                         case WN_F32: e = wn::launch_persist_f32(a, bq, c, full, s->var, smem, s->sms, cs); break;
                         case WN_BF16: e = wn::launch_persist_bf16(a, bq, c, full, s->var, smem, s->sms, cs); break;
@@ -1241,11 +1372,11 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
             const size_t smem = wn::gen_smem_bytes(s->smem_base, g.N, g.r_max);
             for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
                 e = restore();
-                if (e == cudaSuccess) e = cudaMemsetAsync(s->d_queue, 0, sizeof(uint32_t) * 16, cs);
+                if (e == cudaSuccess) e = cudaMemsetAsync(d.queue, 0, sizeof(uint32_t) * 16, cs);
                 if (e == cudaSuccess) e = cudaEventRecord(e0, cs);
                 if (e == cudaSuccess) {
                     wn::GenArgs a{s->d_hdr, s->d_pools, out, 0, 0, g.len, g.N, g.r_max, 0};
-                    wn::BatchArgs bq{s->d_border + g.start, s->d_boffsets, s->d_bcounts, g.len, s->d_queue};
+                    wn::BatchArgs bq{d.order + g.start, d.offsets, d.counts, g.len, d.queue};
                     switch (dtype) {
                     case WN_F32: e = wn::launch_persist_lat_f32(a, bq, lc, lfull, smem, s->sms, cs); break;
                     case WN_BF16: e = wn::launch_persist_lat_bf16(a, bq, lc, lfull, smem, s->sms, cs); break;
@@ -1279,14 +1410,14 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
             const std::vector<Group> gk = plan_batch(s, counts, ord, k);
             if (gk.size() > 16) continue;
             if ((st = ensure_batch_buffers(s, gk.size())) != WN_OK) break;
-            e = cudaMemcpyAsync(s->d_border, ord.data(), sizeof(uint32_t) * s->n, cudaMemcpyHostToDevice, cs);
+            e = cudaMemcpyAsync(d.order, ord.data(), sizeof(uint32_t) * s->n, cudaMemcpyHostToDevice, cs);
             // the groups' CTAs reach the SMs in a different order on every
             // run, so a single replay varies by ~10%: score the median of four
             float times[4] = {0.f, 0.f, 0.f, 0.f};
             for (int rep = 0; rep < 5 && e == cudaSuccess && st == WN_OK; ++rep) {
                 e = restore();
                 if (e == cudaSuccess) e = cudaEventRecord(e0, cs);
-                if (e == cudaSuccess) st = enqueue_batch(s, gk, out, dtype, cs);
+                if (e == cudaSuccess) st = enqueue_batch(s, gk, out, dtype, cs, d);
                 if (e == cudaSuccess) e = cudaEventRecord(e1, cs);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 float ms = 0.f;
@@ -1308,8 +1439,11 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
     if (pool_bak) cudaFree(pool_bak);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    if (e != cudaSuccess) return cuda_fail("wn_autotune_batch", e);
-    if (st != WN_OK) return st;
+    if (e != cudaSuccess || st != WN_OK) {
+        s->group_cfg = old_cfg;
+        s->group_lat = old_lat;
+        return e != cudaSuccess ? cuda_fail("wn_autotune_batch", e) : st;
+    }
     for (auto &kv : chosen) s->group_cfg[kv.first] = kv.second;
     for (auto &kv : chosen_lat) s->group_lat[kv.first] = kv.second;
     s->batch_crit = best_crit;
@@ -1332,6 +1466,15 @@ wn_status wn_generate_batch_noalloc(void *out, const uint64_t *counts, const uin
     WN_CU(cudaGetDevice(&dev));
     if (dev != s->device)
         return fail(WN_EINVAL, "wn_generate_batch_noalloc: the handle's device must be current");
+    {
+        // the call copies from host arrays and advances host bookkeeping as it
+        // is made: a captured copy would replay stale arrays and a replay would
+        // not advance the streams' positions
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        WN_CU(cudaStreamIsCapturing(reinterpret_cast<cudaStream_t>(cuda_stream), &cap));
+        if (cap != cudaStreamCaptureStatusNone)
+            return fail(WN_EINVAL, "wn_generate_batch_noalloc: not allowed while cuda_stream is being captured");
+    }
     unsigned char *scratch = nullptr;
     if ((st = noalloc_scratch(dev, &scratch)) != WN_OK) return st;
     // Plan without heap allocation: pool sizes are powers of two 4..16384

@@ -59,11 +59,14 @@ struct GenArgs {
 // Launch shape: `threads` compute threads (plus the control warp) each owning
 // `qt` quadruples; `maxt` is the instantiation's thread bound; `ip` selects
 // the in-place pool layout (one pool buffer instead of two; see run_stream).
+// `grp` selects the group-mode kernel (wn_group.cuh): `threads` / 32 warps
+// per stream, `qt` quadruples per lane, no control warp, in place.
 struct LaunchCfg {
     int qt;
     int maxt;
     uint32_t threads;
     int ip = 0;
+    int grp = 0;
 };
 
 // Compiled shapes {quadruples per thread, thread bound (compute threads + 32),

@@ -16,7 +16,11 @@ squares and rounded once to FP32, adding O(u).  Hence
 (C_MAX covers the largest of up to 2^32 Gaussian-like errors, about 6.7
 standard deviations, with margin).  P is the number of passes the value's
 block has seen since initialisation: R (W + b + 1) for block b after W
-warm-up blocks.
+warm-up blocks.  The RMS bound is a statement about many values (their mean
+squared error); it is checked from RMS_MIN_VALUES values up, since for a
+handful of values it is a bound of 2 standard deviations on each, which
+chance alone breaks in a few percent of cases.  The per-value bound holds for
+any count.
 """
 import math
 
@@ -25,6 +29,7 @@ import numpy as np
 U = 2.0 ** -24
 C_RMS = 2.0
 C_MAX = 10.0
+RMS_MIN_VALUES = 32
 
 # round-to-nearest unit roundoffs of the 16-bit output types
 U_BF16 = 2.0 ** -8
@@ -53,5 +58,5 @@ def assert_fp32_close(gpu, ref, P, what=""):
         f"{what}: {bad.size} values beyond tolerance; first at {bad[0]}: "
         f"gpu={gpu[bad[0]]!r} oracle={ref[bad[0]]!r} err={err[bad[0]]:.3e} tol={tol[bad[0]]:.3e}")
     rms = math.sqrt(float(np.mean((err / scale) ** 2))) if err.size else 0.0
-    assert rms <= C_RMS, f"{what}: normalised RMS error {rms:.3f} > {C_RMS}"
+    assert err.size < RMS_MIN_VALUES or rms <= C_RMS, f"{what}: normalised RMS error {rms:.3f} > {C_RMS}"
     return rms, float(np.max(err / scale)) if err.size else 0.0

@@ -74,6 +74,57 @@ def test_graph_recaptures_on_new_arguments(wn):
     _check(out.cpu().numpy(), N, R, seeds, counts2, off2, prefix=counts)
 
 
+def test_graph_replay_after_an_eager_call_with_other_arguments(wn):
+    # graph(A) -> eager(B) -> graph(A) on one handle: the eager call uploads
+    # other descriptors, and the cached graph must still serve A (it reads a
+    # copy of its own).  Every range of B lies inside the buffer A uses, so a
+    # graph that replayed B's descriptors would give wrong values, not write
+    # out of bounds.
+    import torch
+    N, R, countsA = _mix(14, seed=17)
+    seeds = np.arange(300, 300 + len(N))
+    offA = packed_offsets(countsA) + 1
+    countsB = countsA[::-1].copy()
+    offB = packed_offsets(countsB) + 3
+    size = int(max(offA[-1] + countsA[-1], offB[-1] + countsB[-1])) + 8
+    h = wn.wn_create_streams(N, R, seeds)
+    out = torch.zeros(size, dtype=torch.float32, device="cuda")
+    wn.wn_generate_batch(out, countsA, offA, h, use_graph=True)
+    torch.cuda.synchronize()
+    _check(out.cpu().numpy(), N, R, seeds, countsA, offA)
+    wn.wn_generate_batch(out, countsB, offB, h, use_graph=False)
+    torch.cuda.synchronize()
+    _check(out.cpu().numpy(), N, R, seeds, countsB, offB, prefix=countsA)
+    out.zero_()
+    wn.wn_generate_batch(out, countsA, offA, h, use_graph=True)  # a replay of the first graph
+    torch.cuda.synchronize()
+    _check(out.cpu().numpy(), N, R, seeds, countsA, offA, prefix=countsA + countsB)
+    for i in range(len(N)):
+        ref = oracle.Stream(int(N[i]), int(R[i]), int(seeds[i]))
+        ref.skip(int(2 * countsA[i] + countsB[i]))
+        st = wn.wn_get_state(h, i)
+        assert (st["k"], st["blocks"]) == (ref.k, ref.blocks)
+
+
+def test_batch_arguments_may_be_reused_at_once(wn):
+    # counts and offsets are copied before the call returns: overwriting the
+    # caller's (page-locked) arrays right after the call changes nothing
+    import torch
+    N, R, counts = _mix(10, seed=23)
+    seeds = np.arange(40, 40 + len(N))
+    offsets = packed_offsets(counts)
+    tc = torch.from_numpy(counts.astype(np.int64)).pin_memory()
+    to = torch.from_numpy(offsets.astype(np.int64)).pin_memory()
+    h = wn.wn_create_streams(N, R, seeds)
+    out = torch.zeros(int(counts.sum()) + 8, dtype=torch.float32, device="cuda")
+    wn._L().wn_generate_batch(out.data_ptr(), tc.data_ptr(), to.data_ptr(), h.ptr, wn.WN_F32, 0,
+                              torch.cuda.current_stream().cuda_stream)
+    tc.fill_(0)
+    to.fill_(0)
+    torch.cuda.synchronize()
+    _check(out.cpu().numpy(), N, R, seeds, counts, offsets)
+
+
 def test_autotune_batch_keeps_state(wn):
     import torch
     N, R, counts = _mix(20, seed=11)

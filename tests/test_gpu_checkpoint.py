@@ -66,6 +66,28 @@ def test_save_includes_enqueued_work_and_matches_oracle(wn):
         assert_fp32_close(got[i], ref.generate(2 * 4095 + 3), passes_fresh(2 * 4095 + 3, NS[i], RS[i], first_block=fb))
 
 
+def test_save_waits_for_work_on_another_cuda_stream(wn):
+    # a call enqueued on a non-blocking stream other than the handle's: the
+    # checkpoint must still include it (one lone stream of 2^24 values takes
+    # milliseconds, so a save that did not wait would copy the old state)
+    import torch
+    h = wn.wn_create(1024, 2, 7)
+    side = torch.cuda.Stream()
+    n = 1 << 24
+    out = torch.empty(n, device="cuda")
+    with torch.cuda.stream(side):
+        wn.wn_generate_ex(out, n, h, wn.WN_F32, side)
+    buf = wn.wn_save(h)  # no synchronisation before it
+    ref = oracle.Stream(1024, 2, 7)
+    ref.skip(n)
+    h2 = wn.wn_load(buf)
+    st = wn.wn_get_state(h2, 0)
+    assert (st["k"], st["blocks"]) == (ref.k, ref.blocks)
+    assert (st["x"], st["w"]) == ref.gen_state
+    torch.cuda.synchronize()
+    assert wn.wn_get_state(h, 0) == st
+
+
 def test_buffer_too_small_is_rejected(wn):
     import ctypes
     h = wn.wn_create_streams([64], [2], [1])

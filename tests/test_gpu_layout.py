@@ -125,13 +125,20 @@ def test_in_place_rejected_where_not_compiled(wn):
     with pytest.raises(wn.WnError):
         wn.wn_set_config_ex(h, 8, 128, wn.WN_CFG_IN_PLACE)  # no in-place kernel with 8 quadruples per thread
     with pytest.raises(wn.WnError):
-        wn.wn_set_config_ex(h, 16, 64, 2)  # unknown flag
+        wn.wn_set_config_ex(h, 16, 64, 4)  # unknown flag
 
 
-def test_large_pools_default_to_in_place(wn):
-    # the library's default shape for pools of 16384 is the in-place one;
-    # pools of 4096 keep two buffers
-    h = wn.wn_create_streams([16384] * 100, [3] * 100, list(range(1, 101)))
-    assert wn.wn_get_config_ex(h) == (16, 256, wn.WN_CFG_IN_PLACE)
-    h2 = wn.wn_create_streams([4096] * 100, [2] * 100, list(range(1, 101)))
+def test_default_shapes(wn):
+    # many streams of one pool size from 1024 up run the group mode by
+    # default (one warp per stream up to 4096, two at 8192, four at 16384);
+    # variants and smaller pools keep the ordinary kernel's shapes
+    GI = wn.WN_CFG_IN_PLACE | wn.WN_CFG_GROUP
+    for N, shape in ((1024, (8, 32, GI)), (4096, (32, 32, GI)), (8192, (32, 64, GI)), (16384, (32, 128, GI))):
+        h = wn.wn_create_streams([N] * 100, [2] * 100, list(range(1, 101)), warmup_blocks=0)
+        assert wn.wn_get_config_ex(h) == shape, N
+    hv = wn.wn_create_ex([16384] * 100, [3] * 100, list(range(1, 101)), warmup_blocks=0, chi2="b")
+    assert wn.wn_get_config_ex(hv) == (16, 256, wn.WN_CFG_IN_PLACE)
+    h2 = wn.wn_create_ex([4096] * 100, [2] * 100, list(range(1, 101)), warmup_blocks=0, chi2="b")
     assert wn.wn_get_config_ex(h2) == (8, 128, 0)
+    h3 = wn.wn_create_streams([256] * 100, [2] * 100, list(range(1, 101)), warmup_blocks=0)
+    assert wn.wn_get_config_ex(h3)[2] == 0

@@ -69,12 +69,12 @@ def test_fp32_precision_config_matches_oracle(wn, refs):
 
 def test_full_precision_launch_sampled(wn, refs):
     # the 16-bit workload in the launch configuration the benchmark times:
-    # 4096 streams x 2^21 BF16 values in one launch (the default in-place
+    # 4096 streams x 2^21 BF16 values in one launch (the default group-mode
     # shape), checked on sampled streams' first 2^20 values
     import torch
     S, per = 4096, 1 << 21
     h = wn.wn_create_streams([N] * S, [R] * S, list(range(1, S + 1)))
-    assert wn.wn_get_config_ex(h) == (16, 256, wn.WN_CFG_IN_PLACE)
+    assert wn.wn_get_config_ex(h) == (32, 128, wn.WN_CFG_IN_PLACE | wn.WN_CFG_GROUP)
     out = torch.empty(S * per, dtype=torch.bfloat16, device="cuda")
     wn.wn_generate_ex(out, per, h, 1)
     torch.cuda.synchronize()

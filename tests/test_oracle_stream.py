@@ -158,3 +158,20 @@ def test_pool_decimation_draw_count():
     assert s.gen_state == ref.gen_state
     with pytest.raises(ValueError):
         oracle.Stream(N, R, seed, decimate=0)
+
+
+def test_finite_pool_covariances_match_the_sphere_closed_forms():
+    # Section 5.6's effect on the oracle's own stream: a squared value and its
+    # next-block descendants (positions fixed by the pass permutations) have
+    # the covariances of a pool on the sphere sum P^2 = N -- energy
+    # (2N - 2 4^R)/(N+2), one descendant (2N 4^-R - 2)/(N+2), a
+    # non-descendant -2/(N+2) -- each within 5 standard errors; here the
+    # -2/(N+2) terms exceed 5 standard errors, so a dropped sphere term fails
+    from _defects import _draws, energy_covariances, expected_covariances
+    N, R, seed, blocks = 256, 1, 31, 60000
+    out = oracle.Stream(N, R, seed).generate(blocks * (N - 1)).reshape(blocks, N - 1)
+    mean, se = energy_covariances(out, N, R, _draws(N, R, seed, blocks))
+    expect = expected_covariances(N, R)
+    assert np.all(np.abs(mean - expect) < 5 * se), (mean, se, expect)
+    assert abs(mean[2]) > 5 * se[2]
+    assert abs(mean[0] - (2.0 - 2.0 * 4.0 ** R / N)) > 5 * se[0] or abs(mean[1] - 2 * 4.0 ** -R) > 5 * se[1]

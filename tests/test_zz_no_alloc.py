@@ -12,7 +12,8 @@ that pytest collects it last.
 import numpy as np
 import pytest
 
-from _parity import C_MAX, U
+import oracle
+from _parity import C_MAX, U, assert_fp32_close, passes_fresh
 from paper_1005_2314_gb300.workloads import packed_offsets
 
 pytestmark = pytest.mark.gpu
@@ -64,3 +65,39 @@ def test_noalloc_rejects_more_streams_than_its_scratch_holds(wn):
     out = torch.zeros(n, dtype=torch.float32, device="cuda")
     with pytest.raises(wn.WnError, match="exceed"):
         wn.wn_generate_batch_noalloc(out, np.ones(n, dtype=np.uint64), np.arange(n, dtype=np.uint64), h)
+
+
+def test_noalloc_matches_the_oracle_directly(wn):
+    # the same requests checked against the FP64 oracle itself, not only
+    # against the other batch entry point, for streams of every pool size
+    import torch
+    N, R, counts, seeds = _requests()
+    offsets = packed_offsets(counts) + 1
+    h = wn.wn_create_streams(N, R, seeds)
+    out = torch.zeros(int(counts.sum()) + 8, dtype=torch.float32, device="cuda")
+    wn.wn_generate_batch_noalloc(out, counts, offsets, h)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    pick = [int(np.flatnonzero((N == n) & (counts > 0))[0]) for n in np.unique(N)]
+    for i in pick + [1, 2]:
+        c = int(counts[i])
+        ref = oracle.Stream(int(N[i]), int(R[i]), int(seeds[i])).generate(c)
+        assert_fp32_close(got[int(offsets[i]): int(offsets[i]) + c], ref, passes_fresh(c, int(N[i]), int(R[i])),
+                          f"stream {i} N={N[i]} R={R[i]}")
+
+
+def test_noalloc_refuses_stream_capture(wn):
+    # the call reads host arrays and advances host positions when it is made,
+    # so recording it into a CUDA graph is refused (nothing is enqueued)
+    import torch
+    h = wn.wn_create_streams([64, 64], [1, 1], [1, 2])
+    out = torch.zeros(256, dtype=torch.float32, device="cuda")
+    x = torch.zeros(4, device="cuda")
+    before = [wn.wn_get_state(h, i) for i in range(2)]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=torch.cuda.Stream()):
+        x.add_(1.0)
+        with pytest.raises(wn.WnError, match="captured"):
+            wn.wn_generate_batch_noalloc(out, [10, 10], [0, 128], h)
+    torch.cuda.synchronize()
+    assert [wn.wn_get_state(h, i) for i in range(2)] == before
