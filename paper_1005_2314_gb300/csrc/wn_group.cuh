@@ -305,8 +305,9 @@ __global__ void __launch_bounds__(32 * G, MINB) group_kernel(GenArgs a)
 
 // Compiled group-mode shapes {pool N, warps per stream G, quadruples per lane
 // QT, minimum CTAs per SM}.
-constexpr int kGroupShapes[][4] = {{1024, 1, 8, 16}, {2048, 1, 16, 12}, {4096, 1, 32, 9},
-                                   {4096, 2, 16, 9}, {8192, 2, 32, 4},  {16384, 4, 32, 3}};
+constexpr int kGroupShapes[][4] = {{1024, 1, 8, 16}, {1024, 4, 2, 8},  {2048, 1, 16, 12}, {4096, 1, 32, 9},
+                                   {4096, 2, 16, 9},  {4096, 4, 8, 6},  {4096, 8, 4, 4},   {8192, 2, 32, 4},
+                                   {16384, 4, 32, 3}, {16384, 8, 16, 2}};
 
 // Resident CTAs per SM for a launch of n_streams streams: the fewest that
 // keeps the number of waves the most the SM holds would give (4096 streams on
@@ -359,6 +360,10 @@ cudaError_t launch_group_t(const GenArgs &a, uint32_t N, uint32_t G, int sms, cu
     case 2048 * 16 + 1: return launch_group_shape<1, 16, 12, OutT>(a, sms, cs, ctas_per_sm);
     case 4096 * 16 + 1: return launch_group_shape<1, 32, 9, OutT>(a, sms, cs, ctas_per_sm);
     case 4096 * 16 + 2: return launch_group_shape<2, 16, 9, OutT>(a, sms, cs, ctas_per_sm);
+    case 4096 * 16 + 4: return launch_group_shape<4, 8, 6, OutT>(a, sms, cs, ctas_per_sm);
+    case 4096 * 16 + 8: return launch_group_shape<8, 4, 4, OutT>(a, sms, cs, ctas_per_sm);
+    case 1024 * 16 + 4: return launch_group_shape<4, 2, 8, OutT>(a, sms, cs, ctas_per_sm);
+    case 16384 * 16 + 8: return launch_group_shape<8, 16, 2, OutT>(a, sms, cs, ctas_per_sm);
     case 8192 * 16 + 2: return launch_group_shape<2, 32, 4, OutT>(a, sms, cs, ctas_per_sm);
     case 16384 * 16 + 4: return launch_group_shape<4, 32, 3, OutT>(a, sms, cs, ctas_per_sm);
     default: return cudaErrorInvalidValue;

@@ -16,7 +16,8 @@ from _parity import assert_fp32_close, passes_fresh
 pytestmark = pytest.mark.gpu
 
 # (pool N, quadruples per lane, threads) of the compiled group shapes
-SHAPES = [(1024, 8, 32), (2048, 16, 32), (4096, 32, 32), (4096, 16, 64), (8192, 32, 64), (16384, 32, 128)]
+SHAPES = [(1024, 8, 32), (1024, 2, 128), (2048, 16, 32), (4096, 32, 32), (4096, 16, 64), (4096, 8, 128),
+          (4096, 4, 256), (8192, 32, 64), (16384, 32, 128), (16384, 16, 256)]
 
 
 def _handle(wn, N, R, seeds, shape):
@@ -112,7 +113,7 @@ def test_group_rejects_other_shapes_and_variants(wn):
     with pytest.raises(wn.WnError):
         wn.wn_set_config_ex(h, 16, 32, wn.WN_CFG_GROUP)   # covers 2048, not 4096
     with pytest.raises(wn.WnError):
-        wn.wn_set_config_ex(h, 8, 128, wn.WN_CFG_GROUP)   # no such compiled shape
+        wn.wn_set_config_ex(h, 8, 96, wn.WN_CFG_GROUP)    # three warps: no such compiled shape
     hv = wn.wn_create_ex([4096] * 2, [2] * 2, [1, 2], chi2="a")
     with pytest.raises(wn.WnError):
         wn.wn_set_config_ex(hv, 32, 32, wn.WN_CFG_GROUP)  # variants keep the general kernels
