@@ -260,12 +260,14 @@ def _timed(torch, stream, flush, fn, reps):
     return t[len(t) // 2]
 
 
-def other_workloads(wn, torch, dev, stream, flush, sm_mhz=None):
+def other_workloads(wn, torch, dev, stream, flush, sm_mhz=None, headline_value=None):
     """The method's other workloads on this GPU, each timed with CUDA events:
     one stream (pool 1024, R=2, 2^24 FP32 in one call); 4096 streams of pool
     16384, R=3, 2^21 values each in BF16 and in FP16 (with Box-Muller at the
-    same shape and type); and the fused GBM consumer (2^20 paths x 252 steps,
-    pool 4096, R=2, normals never written to memory)."""
+    same shape and type); the same 16-bit outputs at the headline's shape
+    (pool 4096, R=2, 2^20 each); the plane-rotation form at that shape; and
+    the fused GBM consumer (2^20 paths x 252 steps, pool 4096, R=2, normals
+    never written to memory)."""
     peak, _ = _peaks()
     res = {}
     # single stream: a serial chain of blocks on one SM
@@ -301,6 +303,38 @@ def other_workloads(wn, torch, dev, stream, flush, sm_mhz=None):
     res["precision"] = prec
     wn.wn_destroy(h3)
     del o3
+    # the 16-bit outputs at the headline's shape (4096 streams x pool 4096,
+    # R = 2, 2^20 values each): what halving the bytes per value buys
+    S2, N2, R2, per2 = 4096, 4096, 2, 1 << 20
+    h2 = wn.wn_create_streams([N2] * S2, [R2] * S2, list(range(1, S2 + 1)), WARMUP_BLOCKS, stream)
+    o2 = torch.empty(S2 * per2, dtype=torch.bfloat16, device=dev)
+    pc2 = {}
+    for dt, name, tdt in ((wn.WN_BF16, "bf16", torch.bfloat16), (wn.WN_F16, "f16", torch.float16)):
+        o = o2.view(tdt)
+        wn.wn_generate_ex(o, per2, h2, dt, stream)
+        t2 = _timed(torch, stream, flush, lambda: wn.wn_generate_ex(o, per2, h2, dt, stream), 5)
+        v = S2 * per2 / (t2 / 1e3)
+        l1 = _l1_roofline(v, R2, 2, sm_mhz, torch.cuda.get_device_properties(dev).multi_processor_count)
+        pc2[name] = {"value": v, "unit": "variates/s", "ms_per_step": t2, "shape": list(wn.wn_get_config_ex(h2)),
+                     "hbm_frac": round(v * 2 / 1e9 / peak, 4), "l1_frac": l1["frac"] if l1 else None,
+                     "over_fp32_headline": round(v / headline_value, 4) if headline_value else None}
+    pc2["config"] = "4096 streams x pool N=4096, R=2, 2^20 values each (2^32 per type), FP32 pool, 16-bit RN output"
+    res["precision_c2"] = pc2
+    # the plane-rotation form (Section 5.3, rann4) at the headline's shape, FP32
+    hr = wn.wn_create_ex([N2] * S2, [R2] * S2, list(range(1, S2 + 1)), WARMUP_BLOCKS, update="rotation",
+                         cuda_stream=stream)
+    o = o2.view(torch.float32)[: S2 * per2 // 2]
+    perr = per2 // 2
+    wn.wn_generate_ex(o, perr, hr, wn.WN_F32, stream)
+    tr = _timed(torch, stream, flush, lambda: wn.wn_generate_ex(o, perr, hr, wn.WN_F32, stream), 5)
+    v = S2 * perr / (tr / 1e3)
+    res["rotation"] = {"value": v, "unit": "variates/s", "ms_per_step": tr, "shape": list(wn.wn_get_config_ex(hr)),
+                       "hbm_frac": round(v * 4 / 1e9 / peak, 4),
+                       "config": "4096 streams x pool N=4096, R=2, 2^19 FP32 values each, plane rotations "
+                                 "(general kernel; gathers 2-way bank-conflicted)"}
+    wn.wn_destroy(hr)
+    wn.wn_destroy(h2)
+    del o2
     # fused consumer: geometric Brownian motion driven in-kernel
     # 585 paths per stream (7 steps per block): 1793 streams, four full waves of
     # 3 CTAs per SM (measured 0.249 ms against 0.263 for 455 per stream, whose
@@ -312,8 +346,12 @@ def other_workloads(wn, torch, dev, stream, flush, sm_mhz=None):
     args5 = (0.05, 0.2, 1.0 / 252)
     wn.wn_gbm(st, h5, ppg, steps, 100.0, *args5, stream)
     t5 = _timed(torch, stream, flush, lambda: wn.wn_gbm(st, h5, ppg, steps, 100.0, *args5, stream), 5)
-    res["gbm"] = {"value": G * ppg * steps / (t5 / 1e3), "unit": "normals consumed/s", "ms_per_call": t5,
-                  "paths_per_s": G * ppg / (t5 / 1e3),
+    gv = G * ppg * steps / (t5 / 1e3)
+    # the consumer writes nothing per value: its bound is the shared-memory
+    # side alone (2R wavefronts per 32 values, no output wavefronts)
+    gl1 = _l1_roofline(gv, R5, 0, sm_mhz, torch.cuda.get_device_properties(dev).multi_processor_count)
+    res["gbm"] = {"value": gv, "unit": "normals consumed/s", "ms_per_call": t5,
+                  "paths_per_s": G * ppg / (t5 / 1e3), "l1_frac": gl1["frac"] if gl1 else None,
                   "config": f"{G * ppg} paths ({G} streams x {ppg}) x 252 steps, pool N=4096, R=2, "
                             "S0=100, mu=0.05, sigma=0.2, dt=1/252"}
     wn.wn_destroy(h5)
@@ -350,7 +388,10 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def step():
-        wn.wn_generate_ex(out, PER_STREAM, h, wdt, stream)
+        if args.method == "boxmuller":  # the comparison generator on the same shape (--kernel-only)
+            wn.wn_boxmuller(out, PER_STREAM, STREAMS, 1, wdt, stream)
+        else:
+            wn.wn_generate_ex(out, PER_STREAM, h, wdt, stream)
 
     for _ in range(args.warmup):
         step()
@@ -389,6 +430,12 @@ def run_ours(args, rank, world, local_rank):
                            f"per lane per stream, no control warp, in-place pool)" if shape[2] & 2 else
                            f"wn::generate_kernel ({DT.upper()} out, {shape[0]} quadruples x {shape[1]} compute "
                            f"threads + 1 control warp per stream{', in-place pool' if shape[2] else ''})")}
+    if args.method == "boxmuller":
+        roofline["kernel"] = f"wn::boxmuller_kernel ({DT.upper()} out, Philox4x32-10)"
+        roofline["algorithmic_bytes_per_launch"] = algo = STREAMS * PER_STREAM * ESIZE[DT]
+        roofline["achieved"] = round(algo / (ms_per_step / 1e3) / 1e9, 1)
+        roofline["frac"] = round(roofline["achieved"] / peak, 4)
+        roofline["traffic"] = None
     if args.kernel_only:
         wn.wn_destroy(h)
         return {"metric": METRIC, "value": value, "unit": "variates/s", "n_gpus": world, "steps": args.steps,
@@ -450,7 +497,7 @@ def run_ours(args, rank, world, local_rank):
     # many-streams FP32 step above)
     configs = None
     if not args.no_configs:
-        configs = other_workloads(wn, torch, dev, stream, flush, clk.summary()["sm_mhz"])
+        configs = other_workloads(wn, torch, dev, stream, flush, clk.summary()["sm_mhz"], value / world)
 
     # the batched uneven-request workload: 10,000 streams, pool from
     # {1024, 4096, 16384}, R from {1, 2, 4}, log-uniform lengths 2^10..2^24,
@@ -468,7 +515,7 @@ def run_ours(args, rank, world, local_rank):
         wn.wn_generate_batch(bout, bc, boff, hb, wn.WN_F32, True, stream)  # captures the graph
         torch.cuda.synchronize()
         bms = []
-        for i in range(3):
+        for i in range(7):
             flush.fill_(i & 0xFF)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -476,14 +523,16 @@ def run_ours(args, rank, world, local_rank):
             b.record(stream)
             bms.append((a, b))
         torch.cuda.synchronize()
-        bt = sorted(x.elapsed_time(y) for x, y in bms)[1]
+        bts = sorted(x.elapsed_time(y) for x, y in bms)
+        bt = bts[len(bts) // 2]
         batched = {"value": btotal / (bt / 1e3), "unit": "variates/s", "ms_per_replay": bt,
-                   "variates_per_replay": btotal, "streams": 10000,
+                   "ms_min": bts[0], "ms_max": bts[-1], "spread": round(bts[-1] / bts[0] - 1, 4),
+                   "replays": len(bts), "variates_per_replay": btotal, "streams": 10000,
                    "achieved_gbs": round(btotal * 4 / (bt / 1e3) / 1e9, 1),
                    "longest_request": int(bc.max()),
                    "how": "wn_generate_batch with use_graph: per pool size one persistent kernel (atomic claim, "
                           "longest request first), groups forked on branch streams, captured once and replayed; "
-                          "launch shapes from wn_autotune_batch; median of 3 replays"}
+                          "launch shapes from wn_autotune_batch; median of 7 replays (min, max and spread beside it)"}
         wn.wn_destroy(hb)
         del bout
 
@@ -557,13 +606,16 @@ def main():
     ap.add_argument("--passes", type=int, default=PASSES_R, help="passes per block R (--kernel-only runs)")
     ap.add_argument("--dtype", choices=sorted(ESIZE), default="f32", help="output type (--kernel-only runs)")
     ap.add_argument("--in-place", action="store_true", help="with --shape: the in-place pool layout")
+    ap.add_argument("--method", choices=["wallace", "boxmuller"], default="wallace",
+                    help="--kernel-only: time Wallace's generator or the Box-Muller comparison on the same shape")
     ap.add_argument("--group", action="store_true",
                     help="with --shape 'quadruples per lane,threads': the group-mode kernel")
     ap.add_argument("--autotune", action="store_true",
                     help="main workload: wn_autotune's pick instead of the library default shape")
     args = ap.parse_args()
-    if (args.pool, args.passes, args.dtype) != (POOL_N, PASSES_R, "f32") and not args.kernel_only:
-        ap.error("--pool/--passes/--dtype select another workload for --kernel-only runs only")
+    if ((args.pool, args.passes, args.dtype) != (POOL_N, PASSES_R, "f32") or args.method != "wallace") \
+            and not args.kernel_only:
+        ap.error("--pool/--passes/--dtype/--method select another workload for --kernel-only runs only")
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

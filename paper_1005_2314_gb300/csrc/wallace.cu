@@ -540,10 +540,40 @@ wn_status ensure_batch_buffers(wn_stream *s, size_t n_groups)
     return WN_OK;
 }
 
-LaunchCfg group_cfg(const wn_stream *s, uint32_t N)
+// Batch groups of one pool size can run the group mode whenever the handle
+// runs the plain method (mixed pool sizes are split into groups anyway).
+bool batch_group_ok(const wn_stream *s) { return !s->var && s->smem_base == wn::kGroupBase; }
+
+// The shape a batch group of pool N runs with: the tuner's pick, else the
+// group mode's default for N, else the ordinary kernel's.
+LaunchCfg batch_cfg(const wn_stream *s, uint32_t N)
 {
     auto it = s->group_cfg.find(N);
-    return it != s->group_cfg.end() ? it->second : pick_cfg(N);
+    if (it != s->group_cfg.end()) return it->second;
+    uint32_t G = 0;
+    if (batch_group_ok(s) && group_default(N, G) && group_shape_ok(N, G)) return group_cfg_of(N, G);
+    return pick_cfg(N);
+}
+
+// One persistent launch of a batch group of pool N with shape c (ordinary or
+// group mode; smem: the ordinary kernel's shared memory).
+cudaError_t launch_persist_cfg(const wn_stream *s, const wn::GenArgs &a, const wn::BatchArgs &bq, const LaunchCfg &c,
+                               uint32_t N, wn_dtype dt, size_t smem, cudaStream_t cs)
+{
+    if (c.grp) {
+        const uint32_t G = c.threads / 32u;
+        switch (dt) {
+        case WN_F32: return wn::launch_persist_group_f32(a, bq, N, G, s->sms, cs);
+        case WN_BF16: return wn::launch_persist_group_bf16(a, bq, N, G, s->sms, cs);
+        default: return wn::launch_persist_group_f16(a, bq, N, G, s->sms, cs);
+        }
+    }
+    const bool full = (uint64_t)c.threads * c.qt == N / 4;
+    switch (dt) {
+    case WN_F32: return wn::launch_persist_f32(a, bq, c, full, s->var, smem, s->sms, cs);
+    case WN_BF16: return wn::launch_persist_bf16(a, bq, c, full, s->var, smem, s->sms, cs);
+    default: return wn::launch_persist_f16(a, bq, c, full, s->var, smem, s->sms, cs);
+    }
 }
 
 // Enqueues a batch whose descriptors are already on the device (in d): reset
@@ -579,8 +609,10 @@ wn_status enqueue_batch(wn_stream *s, const std::vector<Group> &groups, void *ou
         cudaError_t e;
         LaunchCfg lc;
         const auto tuned = s->group_lat.find(g.N);
+        // untuned groups take the latency mode only where the group mode cannot run
         const bool want_lat = g.exclusive ? s->batch_lat >= 1
-                                          : (tuned != s->group_lat.end() ? tuned->second : s->batch_lat >= 2);
+                                          : (tuned != s->group_lat.end() ? tuned->second
+                                                                         : s->batch_lat >= 2 && !batch_cfg(s, g.N).grp);
         if (!s->var && want_lat && latency_default(g.N, lc)) {
             const bool lfull = (uint64_t)lc.threads * lc.qt == g.N / 4;
             switch (dt) {
@@ -593,14 +625,9 @@ wn_status enqueue_batch(wn_stream *s, const std::vector<Group> &groups, void *ou
             WN_CU(cudaStreamWaitEvent(cs, s->join[gi], 0));
             continue;
         }
-        const LaunchCfg c = g.exclusive ? latency_cfg(g.N) : group_cfg(s, g.N);
-        const bool full = (uint64_t)c.threads * c.qt == g.N / 4;
-        if (!g.exclusive) smem = cfg_smem(s, c, g.N, g.r_max);
-        switch (dt) {
-        case WN_F32: e = wn::launch_persist_f32(a, bq, c, full, s->var, smem, s->sms, b); break;
-        case WN_BF16: e = wn::launch_persist_bf16(a, bq, c, full, s->var, smem, s->sms, b); break;
-        default: e = wn::launch_persist_f16(a, bq, c, full, s->var, smem, s->sms, b); break;
-        }
+        const LaunchCfg c = g.exclusive ? latency_cfg(g.N) : batch_cfg(s, g.N);
+        if (!g.exclusive && !c.grp) smem = cfg_smem(s, c, g.N, g.r_max);
+        e = launch_persist_cfg(s, a, bq, c, g.N, dt, smem, b);
         if (e != cudaSuccess) return cuda_fail("wn_generate_batch: launch", e);
         WN_CU(cudaEventRecord(s->join[gi], b));
         WN_CU(cudaStreamWaitEvent(cs, s->join[gi], 0));
@@ -1328,40 +1355,43 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
         const uint32_t nq = g.N / 4;
         float best_ms = 1e30f;
         LaunchCfg best = pick_cfg(g.N);
+        // candidates: the full ordinary shapes and, for the plain method, the
+        // group-mode shapes of this pool size
+        std::vector<LaunchCfg> cand;
         for (const auto &k : wn::kShapes)
-            for (uint32_t t = 32; t + 32 <= (uint32_t)k[1] && e == cudaSuccess; t += 32) {
+            for (uint32_t t = 32; t + 32 <= (uint32_t)k[1]; t += 32) {
                 LaunchCfg c{k[0], k[1], t, k[3]};
-                if (!cfg_ok(c, g.N) || (uint64_t)t * k[0] != nq) continue;  // full shapes only
-                s->group_cfg[g.N] = c;
-                std::vector<Group> one(1, g);
-                float times[2] = {0.f, 0.f};
-                for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
-                    e = restore();
-                    if (e == cudaSuccess) e = cudaMemsetAsync(d.queue, 0, sizeof(uint32_t) * 16, cs);
-                    if (e == cudaSuccess) e = cudaEventRecord(e0, cs);
-                    if (e == cudaSuccess) {
-                        const bool full = true;
-                        const size_t smem = cfg_smem(s, c, g.N, g.r_max);
-                        wn::GenArgs a{s->d_hdr, s->d_pools, out, 0, 0, g.len, g.N, g.r_max, 0};
-                        wn::BatchArgs bq{d.order + g.start, d.offsets, d.counts, g.len, d.queue};
-                        switch (dtype) {
-                        case WN_F32: e = wn::launch_persist_f32(a, bq, c, full, s->var, smem, s->sms, cs); break;
-                        case WN_BF16: e = wn::launch_persist_bf16(a, bq, c, full, s->var, smem, s->sms, cs); break;
-                        default: e = wn::launch_persist_f16(a, bq, c, full, s->var, smem, s->sms, cs); break;
-                        }
-                    }
-                    if (e == cudaSuccess) e = cudaEventRecord(e1, cs);
-                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                    float ms = 0.f;
-                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-                    if (rep > 0) times[rep - 1] = ms;
-                }
-                const float t_ms = std::min(times[0], times[1]);
-                if (e == cudaSuccess && t_ms < best_ms) {
-                    best_ms = t_ms;
-                    best = c;
-                }
+                if (cfg_ok(c, g.N) && (uint64_t)t * k[0] == nq) cand.push_back(c);  // full shapes only
             }
+        if (batch_group_ok(s))
+            for (const auto &k : wn::kGroupShapes)
+                if ((uint32_t)k[0] == g.N) cand.push_back(group_cfg_of(g.N, (uint32_t)k[1]));
+        for (size_t ci = 0; ci < cand.size() && e == cudaSuccess; ++ci) {
+            const LaunchCfg c = cand[ci];
+            s->group_cfg[g.N] = c;
+            float times[2] = {0.f, 0.f};
+            for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+                e = restore();
+                if (e == cudaSuccess) e = cudaMemsetAsync(d.queue, 0, sizeof(uint32_t) * 16, cs);
+                if (e == cudaSuccess) e = cudaEventRecord(e0, cs);
+                if (e == cudaSuccess) {
+                    const size_t smem = cfg_smem(s, c, g.N, g.r_max);
+                    wn::GenArgs a{s->d_hdr, s->d_pools, out, 0, 0, g.len, g.N, g.r_max, 0};
+                    wn::BatchArgs bq{d.order + g.start, d.offsets, d.counts, g.len, d.queue};
+                    e = launch_persist_cfg(s, a, bq, c, g.N, dtype, smem, cs);
+                }
+                if (e == cudaSuccess) e = cudaEventRecord(e1, cs);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) times[rep - 1] = ms;
+            }
+            const float t_ms = std::min(times[0], times[1]);
+            if (e == cudaSuccess && t_ms < best_ms) {
+                best_ms = t_ms;
+                best = c;
+            }
+        }
         chosen[g.N] = best;
         // the latency mode with its default shape, if it beats every ordinary shape
         LaunchCfg lc;
@@ -1518,15 +1548,9 @@ wn_status wn_generate_batch_noalloc(void *out, const uint64_t *counts, const uin
         const uint32_t N = 4u << g;
         wn::GenArgs a{s->d_hdr, s->d_pools, out, 0, 0, cnt[g], N, rmax[g], 0};
         wn::BatchArgs bq{d_order + start[g], d_offsets, d_counts, cnt[g], d_counters + g};
-        const LaunchCfg c = group_cfg(s, N);
-        const bool full = (uint64_t)c.threads * c.qt == N / 4;
+        const LaunchCfg c = batch_cfg(s, N);
         const size_t smem = cfg_smem(s, c, N, rmax[g]);
-        cudaError_t e;
-        switch (dtype) {
-        case WN_F32: e = wn::launch_persist_f32(a, bq, c, full, s->var, smem, s->sms, cs); break;
-        case WN_BF16: e = wn::launch_persist_bf16(a, bq, c, full, s->var, smem, s->sms, cs); break;
-        default: e = wn::launch_persist_f16(a, bq, c, full, s->var, smem, s->sms, cs); break;
-        }
+        const cudaError_t e = launch_persist_cfg(s, a, bq, c, N, dtype, smem, cs);
         if (e != cudaSuccess) return cuda_fail("wn_generate_batch_noalloc: launch", e);
     }
     for (uint32_t i = 0; i < s->n; ++i) advance_k_one(s, i, counts[i]);

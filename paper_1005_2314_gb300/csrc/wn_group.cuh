@@ -370,6 +370,84 @@ cudaError_t launch_group_t(const GenArgs &a, uint32_t N, uint32_t G, int sms, cu
     }
 }
 
+// Persistent group-mode kernel for batches (one pool size): each CTA claims
+// the next stream from an atomic counter (longest request first), returns
+// that stream's request, and claims again until the list is exhausted.  No
+// CTA waits on another.  The claimed index passes through the small area
+// (word 24), since static shared memory would move the pool's window address.
+template <int G, int QT, int MINB, typename OutT>
+__global__ void __launch_bounds__(32 * G, MINB) persist_group_kernel(GenArgs a, BatchArgs bq)
+{
+    uint32_t *slot = reinterpret_cast<uint32_t *>(wn_smem) + 24;
+    for (;;) {
+        group_sync<G>();  // the previous stream is done with shared memory
+        uint32_t it;
+        if (G == 1) {
+            uint32_t c = 0;
+            if (threadIdx.x == 0) c = atomicAdd(bq.queue, 1u);
+            it = __shfl_sync(0xffffffffu, c, 0);
+        } else {
+            if (threadIdx.x == 0) *slot = atomicAdd(bq.queue, 1u);
+            __syncthreads();
+            it = *slot;
+        }
+        if (it >= bq.n_items) return;
+        const uint32_t si = bq.order[it];
+        StreamHdr *h = a.hdr + si;
+        const uint64_t off = bq.offsets[si];
+        run_stream_group<G, QT, OutT>(h, a.pools + h->pool_off, reinterpret_cast<OutT *>(a.out) + off, off,
+                                      bq.counts[si]);
+    }
+}
+
+template <int G, int QT, int MINB, typename OutT>
+cudaError_t launch_persist_group_shape(const GenArgs &a, const BatchArgs &bq, int sms, cudaStream_t cs)
+{
+    auto kern = persist_group_kernel<G, QT, MINB, OutT>;
+    const size_t smem = group_smem_bytes(128u * QT * G);
+    int dev = 0, optin = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * G, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1 || smem > (size_t)optin) return cudaErrorInvalidConfiguration;
+    const uint32_t grid = std::min<uint32_t>(bq.n_items, (uint32_t)(per_sm * sms));
+    if (grid == 0) return cudaSuccess;
+    kern<<<grid, 32 * G, smem, cs>>>(a, bq);
+    return cudaGetLastError();
+}
+
+// Persistent launch of the group-mode kernel for pool N with G warps per
+// stream over the batch list bq.
+template <typename OutT>
+cudaError_t launch_persist_group_t(const GenArgs &a, const BatchArgs &bq, uint32_t N, uint32_t G, int sms,
+                                   cudaStream_t cs)
+{
+    switch (N * 16 + G) {
+    case 1024 * 16 + 1: return launch_persist_group_shape<1, 8, 16, OutT>(a, bq, sms, cs);
+    case 1024 * 16 + 4: return launch_persist_group_shape<4, 2, 8, OutT>(a, bq, sms, cs);
+    case 2048 * 16 + 1: return launch_persist_group_shape<1, 16, 12, OutT>(a, bq, sms, cs);
+    case 4096 * 16 + 1: return launch_persist_group_shape<1, 32, 9, OutT>(a, bq, sms, cs);
+    case 4096 * 16 + 2: return launch_persist_group_shape<2, 16, 9, OutT>(a, bq, sms, cs);
+    case 4096 * 16 + 4: return launch_persist_group_shape<4, 8, 6, OutT>(a, bq, sms, cs);
+    case 4096 * 16 + 8: return launch_persist_group_shape<8, 4, 4, OutT>(a, bq, sms, cs);
+    case 8192 * 16 + 2: return launch_persist_group_shape<2, 32, 4, OutT>(a, bq, sms, cs);
+    case 16384 * 16 + 4: return launch_persist_group_shape<4, 32, 3, OutT>(a, bq, sms, cs);
+    case 16384 * 16 + 8: return launch_persist_group_shape<8, 16, 2, OutT>(a, bq, sms, cs);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_persist_group_f32(const GenArgs &a, const BatchArgs &bq, uint32_t N, uint32_t G, int sms,
+                                     cudaStream_t cs);
+cudaError_t launch_persist_group_bf16(const GenArgs &a, const BatchArgs &bq, uint32_t N, uint32_t G, int sms,
+                                      cudaStream_t cs);
+cudaError_t launch_persist_group_f16(const GenArgs &a, const BatchArgs &bq, uint32_t N, uint32_t G, int sms,
+                                     cudaStream_t cs);
+
 cudaError_t launch_group_f32(const GenArgs &a, uint32_t N, uint32_t G, int sms, cudaStream_t cs,
                              uint32_t *ctas_per_sm);
 cudaError_t launch_group_bf16(const GenArgs &a, uint32_t N, uint32_t G, int sms, cudaStream_t cs,
