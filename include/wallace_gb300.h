@@ -224,6 +224,20 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
                             wn_dtype dtype, void *cuda_stream);
 
 /*
+ * wn_get_batch_plan / wn_set_batch_plan -- how wn_generate_batch treats the
+ * batch's longest serial chains (a stream is a serial chain of blocks,
+ * Section 5.1): `chains` requests, longest first, run in the latency mode in
+ * chain groups launched ahead of the others, at most `density` chain CTAs per
+ * SM (1: each has an SM to itself); chains = -1 lets an estimate decide,
+ * 0 uses none.  wn_autotune_batch sets both by timing the whole batch;
+ * wn_set_batch_plan overrides them (and drops a captured graph).  WN_EINVAL
+ * for chains < -1 or density outside [1, 8].  The plan changes only where
+ * and when streams run, never their values.
+ */
+wn_status wn_get_batch_plan(const wn_stream *s, int32_t *chains, uint32_t *density);
+wn_status wn_set_batch_plan(wn_stream *s, int32_t chains, uint32_t density);
+
+/*
  * wn_gbm -- a fused Monte Carlo consumer: geometric Brownian motion terminal
  * prices driven by the streams' own normals, which never leave the chip.
  * Stream i serves paths [i*paths_per_stream, (i+1)*paths_per_stream); path p

@@ -1,0 +1,16 @@
+// emit_f16.cu -- the latency-mode kernels (emitter warp) instantiated for __half
+// output (a translation unit of its own, so it compiles in parallel).
+#include "wn_emit.cuh"
+
+namespace wn {
+cudaError_t launch_emit_f16(const GenArgs &a, const LaunchCfg &c, bool full, size_t smem, cudaStream_t cs)
+{
+    return launch_emit_t<__half>(a, c, full, smem, cs);
+}
+
+cudaError_t launch_persist_emit_f16(const GenArgs &a, const BatchArgs &bq, const LaunchCfg &c, bool full, size_t smem,
+                                    int sms, cudaStream_t cs)
+{
+    return launch_persist_emit_t<__half>(a, bq, c, full, smem, sms, cs);
+}
+}  // namespace wn

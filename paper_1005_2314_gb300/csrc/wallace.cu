@@ -15,6 +15,7 @@
 #include "wallace_gb300.h"
 #include "wn_gen.cuh"
 #include "wn_group.cuh"
+#include "wn_emit.cuh"
 
 namespace wn {
 
@@ -155,9 +156,12 @@ struct wn_stream {
     // every group whose pool size has a latency shape (2); 0: never.  The
     // batch tuner's choice per pool size (group_lat) overrides it.
     int batch_lat = 2;
-    // batches: how many of the longest serial chains get exclusive groups, as
-    // timed on the whole batch by wn_autotune_batch (-1: the estimate's rule)
+    // batches: how many of the longest serial chains get chain groups (the
+    // latency mode), as timed on the whole batch by wn_autotune_batch (-1: the
+    // estimate's rule), and how many chain CTAs share an SM (1: exclusive)
     int batch_crit = -1;
+    int batch_density = 1;
+    int sm_smem = 0, smem_reserved = 0;  // shared memory per SM and reserved per CTA
     std::map<uint32_t, bool> group_lat;
     // some stream runs a method variant (wn_create_ex, wn_load): use the
     // kernels that read StreamHdr::variant (the others compile the plain method)
@@ -316,6 +320,7 @@ bool latency_default(uint32_t n_max, LaunchCfg &out)
 bool latency_cfg_for(const wn_stream *s, LaunchCfg &out, uint32_t n_launch)
 {
     if (s->var || n_launch > (uint32_t)std::max(1, s->sms / 2)) return false;
+    if (s->r_max >= 3 && wn::emit_smem_bytes(s->smem_base, s->n_max, s->r_max) > (size_t)s->smem_optin) return false;
     if (s->has_cfg) {
         if (!fits_latency(s->cfg, s->n_max)) return false;
         out = s->cfg;
@@ -342,12 +347,18 @@ wn_status launch_generate(wn_stream *s, void *out, uint64_t count, uint32_t warm
     cudaError_t e;
     LaunchCfg lc;
     if (warmup == 0 && count > 0 && latency_cfg_for(s, lc, a.n_streams)) {
-        const size_t smem = wn::gen_smem_bytes(s->smem_base, s->n_max, s->r_max);
+        // the two-control-warp kernel up to two passes per block, the emitter
+        // kernel (wn_emit.cuh) above (see launch_persist_latency)
+        const bool emit = s->r_max >= 3;
+        const size_t smem = emit ? wn::emit_smem_bytes(s->smem_base, s->n_max, s->r_max)
+                                 : wn::gen_smem_bytes(s->smem_base, s->n_max, s->r_max);
         const bool full = s->uniform_N && (uint64_t)lc.threads * lc.qt == s->n_max / 4;
         switch (dt) {
-        case WN_F32: e = wn::launch_latency_f32(a, lc, full, smem, cs); break;
-        case WN_BF16: e = wn::launch_latency_bf16(a, lc, full, smem, cs); break;
-        case WN_F16: e = wn::launch_latency_f16(a, lc, full, smem, cs); break;
+        case WN_F32: e = emit ? wn::launch_emit_f32(a, lc, full, smem, cs) : wn::launch_latency_f32(a, lc, full, smem, cs); break;
+        case WN_BF16:
+            e = emit ? wn::launch_emit_bf16(a, lc, full, smem, cs) : wn::launch_latency_bf16(a, lc, full, smem, cs);
+            break;
+        case WN_F16: e = emit ? wn::launch_emit_f16(a, lc, full, smem, cs) : wn::launch_latency_f16(a, lc, full, smem, cs); break;
         default: return fail(WN_EINVAL, "unknown dtype");
         }
         if (e != cudaSuccess) return cuda_fail("generate launch (latency mode)", e);
@@ -576,6 +587,45 @@ cudaError_t launch_persist_cfg(const wn_stream *s, const wn::GenArgs &a, const w
     }
 }
 
+// Shared memory of a chain group's CTA (need: the kernel's own): padded so
+// that at most s->batch_density of them share an SM (1: a whole SM each).
+size_t chain_smem(const wn_stream *s, size_t need)
+{
+    size_t pad = (size_t)s->smem_optin;
+    if (s->batch_density > 1 && s->sm_smem > 0)
+        pad = ((size_t)s->sm_smem / (size_t)s->batch_density - (size_t)s->smem_reserved) / 128 * 128;
+    return std::min(std::max(need, pad), (size_t)s->smem_optin);
+}
+
+// One persistent latency-mode launch over a batch group of pool N.  A chain
+// group (chain: padded to batch_density CTAs per SM) with more than two
+// passes per block runs the emitter kernel (wn_emit.cuh; lone streams of
+// pool 1024: 700 ns per block at R = 4 against 790), everything else the
+// two-control-warp kernel (565 / 574 ns at R = 1 / 2 against 594 / 625),
+// which also holds more CTAs per SM: the emitter kernel is built for one CTA
+// per SM (its registers), too few for a group of many streams.
+cudaError_t launch_persist_latency(const wn_stream *s, const wn::GenArgs &a, const wn::BatchArgs &bq,
+                                   const LaunchCfg &lc, uint32_t N, uint32_t r_max, bool chain, wn_dtype dt,
+                                   cudaStream_t cs)
+{
+    const bool lfull = (uint64_t)lc.threads * lc.qt == N / 4;
+    const bool emit = chain && r_max >= 3;
+    size_t smem = emit ? wn::emit_smem_bytes(s->smem_base, N, r_max) : wn::gen_smem_bytes(s->smem_base, N, r_max);
+    if (chain) smem = chain_smem(s, smem);
+    if (emit) {
+        switch (dt) {
+        case WN_F32: return wn::launch_persist_emit_f32(a, bq, lc, lfull, smem, s->sms, cs);
+        case WN_BF16: return wn::launch_persist_emit_bf16(a, bq, lc, lfull, smem, s->sms, cs);
+        default: return wn::launch_persist_emit_f16(a, bq, lc, lfull, smem, s->sms, cs);
+        }
+    }
+    switch (dt) {
+    case WN_F32: return wn::launch_persist_lat_f32(a, bq, lc, lfull, smem, s->sms, cs);
+    case WN_BF16: return wn::launch_persist_lat_bf16(a, bq, lc, lfull, smem, s->sms, cs);
+    default: return wn::launch_persist_lat_f16(a, bq, lc, lfull, smem, s->sms, cs);
+    }
+}
+
 // Enqueues a batch whose descriptors are already on the device (in d): reset
 // the claim counters, fork one branch per group, launch each group's
 // persistent kernel, join.
@@ -605,7 +655,7 @@ wn_status enqueue_batch(wn_stream *s, const std::vector<Group> &groups, void *ou
         bq.n_items = g.len;
         bq.queue = d.queue + gi;
         size_t smem = wn::gen_smem_bytes(s->smem_base, g.N, g.r_max);
-        if (g.exclusive) smem = std::max(smem, (size_t)s->smem_optin);  // nothing else fits on its SM
+        if (g.exclusive) smem = chain_smem(s, smem);  // at most batch_density chain CTAs per SM
         cudaError_t e;
         LaunchCfg lc;
         const auto tuned = s->group_lat.find(g.N);
@@ -614,12 +664,7 @@ wn_status enqueue_batch(wn_stream *s, const std::vector<Group> &groups, void *ou
                                           : (tuned != s->group_lat.end() ? tuned->second
                                                                          : s->batch_lat >= 2 && !batch_cfg(s, g.N).grp);
         if (!s->var && want_lat && latency_default(g.N, lc)) {
-            const bool lfull = (uint64_t)lc.threads * lc.qt == g.N / 4;
-            switch (dt) {
-            case WN_F32: e = wn::launch_persist_lat_f32(a, bq, lc, lfull, smem, s->sms, b); break;
-            case WN_BF16: e = wn::launch_persist_lat_bf16(a, bq, lc, lfull, smem, s->sms, b); break;
-            default: e = wn::launch_persist_lat_f16(a, bq, lc, lfull, smem, s->sms, b); break;
-            }
+            e = launch_persist_latency(s, a, bq, lc, g.N, g.r_max, g.exclusive, dt, b);
             if (e != cudaSuccess) return cuda_fail("wn_generate_batch: launch", e);
             WN_CU(cudaEventRecord(s->join[gi], b));
             WN_CU(cudaStreamWaitEvent(cs, s->join[gi], 0));
@@ -724,6 +769,9 @@ wn_stream *alloc_handle(uint32_t n_streams, const uint32_t *pool_N, const uint32
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&s->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, s->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&s->smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, s->device);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_hdr, sizeof(wn::StreamHdr) * n_streams);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_pools, sizeof(float) * off);
     if (e != cudaSuccess) {
@@ -1398,8 +1446,6 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
         bool lat = false;
         if (e == cudaSuccess && !s->var && latency_default(g.N, lc)) {
             float times[2] = {0.f, 0.f};
-            const bool lfull = (uint64_t)lc.threads * lc.qt == nq;
-            const size_t smem = wn::gen_smem_bytes(s->smem_base, g.N, g.r_max);
             for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
                 e = restore();
                 if (e == cudaSuccess) e = cudaMemsetAsync(d.queue, 0, sizeof(uint32_t) * 16, cs);
@@ -1407,11 +1453,7 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
                 if (e == cudaSuccess) {
                     wn::GenArgs a{s->d_hdr, s->d_pools, out, 0, 0, g.len, g.N, g.r_max, 0};
                     wn::BatchArgs bq{d.order + g.start, d.offsets, d.counts, g.len, d.queue};
-                    switch (dtype) {
-                    case WN_F32: e = wn::launch_persist_lat_f32(a, bq, lc, lfull, smem, s->sms, cs); break;
-                    case WN_BF16: e = wn::launch_persist_lat_bf16(a, bq, lc, lfull, smem, s->sms, cs); break;
-                    default: e = wn::launch_persist_lat_f16(a, bq, lc, lfull, smem, s->sms, cs); break;
-                    }
+                    e = launch_persist_latency(s, a, bq, lc, g.N, g.r_max, false, dtype, cs);
                 }
                 if (e == cudaSuccess) e = cudaEventRecord(e1, cs);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -1426,16 +1468,24 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
     // Then the whole batch with the chosen shapes, for several numbers of
     // exclusive chains (0 .. a third of the SMs, and the estimate's rule):
     // the groups share the machine, which timing them alone cannot show.
-    int best_crit = -1;
+    int best_crit = -1, best_density = 1;
+    const int old_density = s->batch_density;
     if (e == cudaSuccess) {
         for (auto &kv : chosen) s->group_cfg[kv.first] = kv.second;
         for (auto &kv : chosen_lat) s->group_lat[kv.first] = kv.second;
+        // (chains, chain CTAs per SM): the estimate's rule and up to a third of
+        // the SMs exclusively, as before; then more chains sharing SMs two or
+        // four to one, up to as many as that leaves room for
+        std::vector<std::pair<int, int>> cands = {{-1, 1}, {0, 1}};
         const int third = std::max(1, s->sms / 3);
-        std::vector<int> ks = {-1, 0};
-        for (int k = 4; k < third; k *= 2) ks.push_back(k);
-        ks.push_back(third);
+        for (int k = 4; k < third; k *= 2) cands.push_back({k, 1});
+        cands.push_back({third, 1});
+        for (int dd : {2, 4})
+            for (int k = 32; k <= dd * s->sms && k <= (int)s->n; k *= 2) cands.push_back({k, dd});
         float best_ms = 1e30f;
-        for (int k : ks) {
+        for (const auto &cd : cands) {
+            const int k = cd.first;
+            s->batch_density = cd.second;
             std::vector<uint32_t> ord;
             const std::vector<Group> gk = plan_batch(s, counts, ord, k);
             if (gk.size() > 16) continue;
@@ -1460,9 +1510,11 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
             if (t_ms < best_ms) {
                 best_ms = t_ms;
                 best_crit = k;
+                best_density = cd.second;
             }
         }
     }
+    s->batch_density = old_density;
     if (e == cudaSuccess) e = restore();
     if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
     if (hdr_bak) cudaFree(hdr_bak);
@@ -1477,6 +1529,7 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
     for (auto &kv : chosen) s->group_cfg[kv.first] = kv.second;
     for (auto &kv : chosen_lat) s->group_lat[kv.first] = kv.second;
     s->batch_crit = best_crit;
+    s->batch_density = best_density;
     if (s->gexec) {  // a captured graph used the old shapes
         cudaGraphExecDestroy(s->gexec);
         s->gexec = nullptr;
@@ -1554,6 +1607,28 @@ wn_status wn_generate_batch_noalloc(void *out, const uint64_t *counts, const uin
         if (e != cudaSuccess) return cuda_fail("wn_generate_batch_noalloc: launch", e);
     }
     for (uint32_t i = 0; i < s->n; ++i) advance_k_one(s, i, counts[i]);
+    return WN_OK;
+}
+
+wn_status wn_get_batch_plan(const wn_stream *s, int32_t *chains, uint32_t *density)
+{
+    if (!s) return fail(WN_EINVAL, "wn_get_batch_plan: NULL handle");
+    if (chains) *chains = s->batch_crit;
+    if (density) *density = (uint32_t)s->batch_density;
+    return WN_OK;
+}
+
+wn_status wn_set_batch_plan(wn_stream *s, int32_t chains, uint32_t density)
+{
+    if (!s) return fail(WN_EINVAL, "wn_set_batch_plan: NULL handle");
+    if (chains < -1 || density < 1 || density > 8)
+        return fail(WN_EINVAL, "wn_set_batch_plan: chains must be >= -1 and density in [1, 8]");
+    s->batch_crit = chains;
+    s->batch_density = (int)density;
+    if (s->gexec) {  // a captured graph used the old plan
+        cudaGraphExecDestroy(s->gexec);
+        s->gexec = nullptr;
+    }
     return WN_OK;
 }
 

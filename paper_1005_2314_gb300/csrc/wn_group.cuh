@@ -106,6 +106,19 @@ __device__ __forceinline__ float group_scale(double ss, float r, float A, float 
     return __fsqrt_rn(1.0f + u) * c;
 }
 
+// The same scale from a sum of squares held in FP32: ss (1/N) is then exact
+// (N a power of two) and ss/N - 1 exact by Sterbenz's lemma (ss/N lies in
+// [1/2, 2]), so one FP32 FMA gives the deviation the FP64 route rounds to,
+// bit for bit, without FP64's latency.
+__device__ __forceinline__ float group_scale_f32(float ss, float r, float A, float B, uint32_t N)
+{
+    const float invNf = 1.0f / (float)N;
+    const float delta = fmaf(ss, invNf, -1.0f);
+    const float c = __frsqrt_rn(1.0f + delta);
+    const float u = fmaf(A, fmaf(r, r, -1.0f), B * r) * invNf;
+    return __fsqrt_rn(1.0f + u) * c;
+}
+
 // The final pass's output: y (this thread's quadruples q0 + 32 j, unscaled)
 // times sc to ob[4q + k], as in the ordinary kernel's EMIT_WHOLE (A = element
 // offset of ob from a 16-byte boundary) or, with PART, the first n values
