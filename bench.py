@@ -38,6 +38,8 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# every run times the library's tuners afresh (no choices from earlier processes)
+os.environ["WN_TUNE_CACHE"] = "off"
 
 METRIC = "N(0,1) variates/s on 1 GB300, % of HBM-write roofline, vs Box–Muller same GPU"
 STREAMS, POOL_N, PASSES_R, PER_STREAM = 4096, 4096, 2, 1 << 20

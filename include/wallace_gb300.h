@@ -215,10 +215,12 @@ wn_status wn_generate_batch_noalloc(void *out, const uint64_t *counts, const uin
  * fastest, timing each group alone; then times the whole batch with those
  * shapes for several numbers of exclusive groups (the longest serial chains,
  * one CTA per SM: none, 4, 8, ... up to a third of the SMs, or the
- * estimate's rule) and keeps the fastest.  All timing runs on a saved copy of
- * the state (the streams' sequences are unaffected; `out` is overwritten
- * with scratch values).  Later wn_generate_batch calls use the choices.
- * Synchronous.
+ * estimate's rule) and keeps the fastest; it also tries more chain groups
+ * sharing SMs two or four to one (see wn_set_batch_plan).  All timing runs on
+ * a saved copy of the state (the streams' sequences are unaffected; `out` is
+ * overwritten with scratch values).  Later wn_generate_batch calls use the
+ * choices.  A batch tuned before on this device (the tune cache, see
+ * wn_autotune) takes its cached choices without timing.  Synchronous.
  */
 wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *offsets, wn_stream *s,
                             wn_dtype dtype, void *cuda_stream);
@@ -306,8 +308,20 @@ wn_status wn_set_config_ex(wn_stream *s, uint32_t quads_per_thread, uint32_t thr
  * unaffected: the state is restored afterwards).  The chosen shape is
  * returned through quads_per_thread and threads (either may be NULL).  A
  * result is remembered per (streams, largest pool, passes, dtype, count) for
- * the process.  Synchronous; allocates a temporary output of
- * n_streams * count elements and a copy of the state.
+ * the process, and kept across processes in the tune cache (below).
+ * Synchronous; allocates a temporary output of n_streams * count elements and
+ * a copy of the state.
+ *
+ * The tune cache: a small JSON file of the tuners' choices, keyed by the
+ * device's name and SM count and the workload (pool size, passes, stream
+ * count, output type, method variant; for batches a hash of every stream's
+ * pool size, passes and request length), at $WN_TUNE_CACHE if that is set
+ * ("off": no file), else $XDG_CACHE_HOME/wn/tune.json, else
+ * $HOME/.cache/wn/tune.json.  wn_create, wn_create_streams and wn_create_ex
+ * apply the FP32 shape cached for their workload; wn_autotune and
+ * wn_autotune_batch use a cached choice instead of timing (and write the
+ * choices they time).  Entries naming shapes this library did not compile,
+ * and unreadable files, are ignored.
  */
 wn_status wn_autotune(wn_stream *s, uint64_t count, wn_dtype dtype, void *cuda_stream,
                       uint32_t *quads_per_thread, uint32_t *threads);

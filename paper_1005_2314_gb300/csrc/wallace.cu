@@ -16,6 +16,7 @@
 #include "wn_gen.cuh"
 #include "wn_group.cuh"
 #include "wn_emit.cuh"
+#include "tune_cache.h"
 
 namespace wn {
 
@@ -327,6 +328,65 @@ bool latency_cfg_for(const wn_stream *s, LaunchCfg &out, uint32_t n_launch)
         return true;
     }
     return latency_default(s->n_max, out);
+}
+
+// --- the autotuners' choices across processes (tune_cache.cu) -------------
+// The device's name and SM count, the first part of every key.
+std::string device_tag(const wn_stream *s)
+{
+    static std::mutex mu;
+    static std::map<int, std::string> names;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = names.find(s->device);
+    if (it == names.end()) {
+        cudaDeviceProp p{};
+        std::string nm = "unknown";
+        if (cudaGetDeviceProperties(&p, s->device) == cudaSuccess) nm = p.name;
+        for (char &c : nm)
+            if (c == ' ' || c == '"' || c == '|' || c == '\\') c = '_';
+        it = names.emplace(s->device, nm).first;
+    }
+    return it->second + "|sms=" + std::to_string(s->sms);
+}
+
+std::string cfg_text(const LaunchCfg &c)
+{
+    char b[96];
+    std::snprintf(b, sizeof b, "%d %d %u %d %d", c.qt, c.maxt, c.threads, c.ip, c.grp);
+    return b;
+}
+
+bool cfg_from_text(const char *t, LaunchCfg &c)
+{
+    unsigned th = 0;
+    if (std::sscanf(t, "%d %d %u %d %d", &c.qt, &c.maxt, &th, &c.ip, &c.grp) != 5) return false;
+    c.threads = th;
+    return true;
+}
+
+// A shape read from the file is used only if this library compiled it.
+bool cached_cfg_ok(const LaunchCfg &c, uint32_t N)
+{
+    if (c.grp) return c.threads % 32 == 0 && group_shape_ok(N, c.threads / 32u) && c.ip == 1 &&
+                      (uint64_t)128u * c.qt * (c.threads / 32u) == N;
+    return cfg_ok(c, N);
+}
+
+// Key of a handle's generate shape for output type dt.
+std::string gen_key(const wn_stream *s, wn_dtype dt)
+{
+    return "gen|" + device_tag(s) + "|N=" + std::to_string(s->n_max) + "|R=" + std::to_string(s->r_max) +
+           "|uniform=" + std::to_string((int)s->uniform_N) + "|var=" + std::to_string((int)s->var) +
+           "|streams=" + std::to_string(s->n) + "|dtype=" + std::to_string((int)dt);
+}
+
+// The cached generate shape of the handle for dt, if any and valid.
+bool cached_gen_cfg(const wn_stream *s, wn_dtype dt, LaunchCfg &c)
+{
+    std::string v;
+    if (!wn::tune_cache_get(gen_key(s, dt), v) || !cfg_from_text(v.c_str(), c) || !cached_cfg_ok(c, s->n_max))
+        return false;
+    return !c.grp || group_eligible(s);
 }
 
 // One generate launch over streams [first, first + len) of the handle (all of
@@ -866,6 +926,11 @@ wn_stream *wn_create_ex(uint32_t n_streams, const uint32_t *pool_N, const uint32
         wn_destroy(s);
         return nullptr;
     }
+    LaunchCfg c;
+    if (cached_gen_cfg(s, WN_F32, c)) {  // a shape wn_autotune chose for this workload before
+        s->cfg = c;
+        s->has_cfg = true;
+    }
     return s;
 }
 
@@ -1091,6 +1156,16 @@ wn_status wn_autotune(wn_stream *s, uint64_t count, wn_dtype dtype, void *cuda_s
             return WN_OK;
         }
     }
+    {
+        LaunchCfg c;
+        if (cached_gen_cfg(s, dtype, c)) {  // chosen for this workload by an earlier process
+            s->cfg = c;
+            s->has_cfg = true;
+            if (quads_per_thread) *quads_per_thread = (uint32_t)c.qt;
+            if (threads) *threads = c.threads;
+            return WN_OK;
+        }
+    }
     // candidate shapes: every compiled one whose compute threads cover the
     // largest pool with at most twice the needed quadruple slots
     std::vector<LaunchCfg> cand;
@@ -1180,6 +1255,7 @@ wn_status wn_autotune(wn_stream *s, uint64_t count, wn_dtype dtype, void *cuda_s
         std::lock_guard<std::mutex> lock(mu);
         cache[key] = best;
     }
+    wn::tune_cache_put(gen_key(s, dtype), cfg_text(best));
     if (quads_per_thread) *quads_per_thread = (uint32_t)best.qt;
     if (threads) *threads = best.threads;
     return WN_OK;
@@ -1363,11 +1439,78 @@ wn_status wn_generate_batch(void *out, const uint64_t *counts, const uint64_t *o
     return WN_OK;
 }
 
+namespace {
+// Key of a batch's tuned plan: the device, the output type and a hash of
+// every stream's pool size, passes and request length.
+std::string batch_key(const wn_stream *s, const uint64_t *counts, wn_dtype dt)
+{
+    uint64_t h = 0xcbf29ce484222325ull;
+    auto mix = [&](uint64_t v) {
+        for (int i = 0; i < 8; ++i) h = (h ^ ((v >> (8 * i)) & 0xFF)) * 0x100000001b3ull;
+    };
+    for (uint32_t i = 0; i < s->n; ++i) {
+        mix(s->N[i]);
+        mix(s->R[i]);
+        mix(counts[i]);
+    }
+    char hx[32];
+    std::snprintf(hx, sizeof hx, "%016llx", (unsigned long long)h);
+    return "batch|" + device_tag(s) + "|var=" + std::to_string((int)s->var) + "|dtype=" + std::to_string((int)dt) +
+           "|streams=" + std::to_string(s->n) + "|sig=" + hx;
+}
+
+// "chains density;N qt maxt threads ip grp lat;..." <-> the handle's batch choices.
+std::string batch_text(const wn_stream *s)
+{
+    std::string t = std::to_string(s->batch_crit) + " " + std::to_string(s->batch_density);
+    for (const auto &kv : s->group_cfg) {
+        const auto lat = s->group_lat.find(kv.first);
+        t += ";" + std::to_string(kv.first) + " " + cfg_text(kv.second) + " " +
+             std::to_string(lat != s->group_lat.end() && lat->second ? 1 : 0);
+    }
+    return t;
+}
+
+bool batch_from_text(wn_stream *s, const std::string &t)
+{
+    int crit = 0, dens = 0;
+    if (std::sscanf(t.c_str(), "%d %d", &crit, &dens) != 2 || crit < -1 || dens < 1 || dens > 8) return false;
+    std::map<uint32_t, LaunchCfg> cfg;
+    std::map<uint32_t, bool> lat;
+    for (size_t p = t.find(';'); p != std::string::npos; p = t.find(';', p + 1)) {
+        unsigned N = 0;
+        int l = 0, used = 0;
+        if (std::sscanf(t.c_str() + p + 1, "%u%n", &N, &used) != 1 || !valid_pool(N)) return false;
+        LaunchCfg c;
+        const char *rest = t.c_str() + p + 1 + used;
+        if (!cfg_from_text(rest, c) || !cached_cfg_ok(c, N) || (c.grp && !batch_group_ok(s))) return false;
+        if (std::sscanf(rest, "%*d %*d %*u %*d %*d %d", &l) != 1) return false;
+        cfg[N] = c;
+        lat[N] = l != 0;
+    }
+    s->batch_crit = crit;
+    s->batch_density = dens;
+    s->group_cfg = cfg;
+    s->group_lat = lat;
+    return true;
+}
+}  // namespace
+
 wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *offsets, wn_stream *s, wn_dtype dtype,
                             void *cuda_stream)
 {
     wn_status st = check_batch_args(s, out, counts, offsets, dtype);
     if (st != WN_OK) return st;
+    {
+        std::string v;  // tuned for this batch by an earlier process
+        if (wn::tune_cache_get(batch_key(s, counts, dtype), v) && batch_from_text(s, v)) {
+            if (s->gexec) {
+                cudaGraphExecDestroy(s->gexec);
+                s->gexec = nullptr;
+            }
+            return WN_OK;
+        }
+    }
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(cuda_stream);
     std::vector<uint32_t> order;
     const std::vector<Group> groups = plan_batch(s, counts, order, -1);
@@ -1530,6 +1673,7 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
     for (auto &kv : chosen_lat) s->group_lat[kv.first] = kv.second;
     s->batch_crit = best_crit;
     s->batch_density = best_density;
+    wn::tune_cache_put(batch_key(s, counts, dtype), batch_text(s));
     if (s->gexec) {  // a captured graph used the old shapes
         cudaGraphExecDestroy(s->gexec);
         s->gexec = nullptr;

@@ -12,6 +12,12 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# the library's tune cache goes to a file of this test session, never to the
+# user's cache directory (tests that need another file set their own)
+if "WN_TUNE_CACHE" not in os.environ:
+    import tempfile
+    os.environ["WN_TUNE_CACHE"] = os.path.join(tempfile.mkdtemp(prefix="wn_tests_"), "tune.json")
+
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU and the compiled CUDA library")
