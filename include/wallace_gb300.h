@@ -401,6 +401,19 @@ wn_status wn_rng_draws(uint64_t seed, uint64_t n, uint64_t *host_out);
 wn_status wn_boxmuller(void *out, uint64_t count, uint32_t n_streams, uint64_t seed,
                        wn_dtype dtype, void *cuda_stream);
 
+/*
+ * wn_debug_report -- the debug build's bounds record.  A library built with
+ * -DWN_DEBUG (build(debug=True): libwallace_gb300_debug.so) checks every pool
+ * access of the generator kernels' passes, emission and pool loads against
+ * the CTA's dynamic shared memory (window address and alignment) and every
+ * output store against its stream's range; a violation is counted, the first
+ * one's kind and address kept (*host_first = kind << 56 | address, kind 1:
+ * shared window address, 2: global address) and the access skipped -- nothing
+ * traps.  Synchronises the device; reset != 0 clears the record afterwards.
+ * Other builds return WN_EINVAL (and zeros).
+ */
+wn_status wn_debug_report(uint64_t *host_violations, uint64_t *host_first, int reset);
+
 /* wn_last_error -- text of the last error on the calling thread ("" if none). */
 const char *wn_last_error(void);
 

@@ -27,7 +27,7 @@ __all__ = [
     "wn_set_cuda_stream", "wn_set_config", "wn_get_config", "wn_set_config_ex", "wn_get_config_ex",
     "WN_CFG_IN_PLACE", "WN_CFG_GROUP", "wn_autotune", "wn_gbm", "wn_generate_batch",
     "wn_autotune_batch", "wn_generate_batch_noalloc", "wn_get_batch_plan", "wn_set_batch_plan", "wn_num_streams", "wn_get_pool", "wn_get_state",
-    "wn_rng_draws", "wn_boxmuller", "wn_save", "wn_load", "wn_last_error", "library_path", "load",
+    "wn_rng_draws", "wn_debug_report", "wn_boxmuller", "wn_save", "wn_load", "wn_last_error", "library_path", "load",
 ]
 
 WN_F32, WN_BF16, WN_F16 = 0, 1, 2
@@ -44,15 +44,18 @@ class WnError(RuntimeError):
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library this binding loads: $WN_LIBRARY if set (e.g. the debug
+    build, build.LIB_DEBUG), else the in-tree build."""
+    return os.environ.get("WN_LIBRARY") or _build.LIB
 
 
 def _load() -> ctypes.CDLL:
-    if not os.path.exists(_build.LIB):
+    path = library_path()
+    if not os.path.exists(path):
         raise ImportError(
-            f"CUDA library {_build.LIB} is missing: build it with "
+            f"CUDA library {path} is missing: build it with "
             "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
-    L = ctypes.CDLL(_build.LIB)
+    L = ctypes.CDLL(path)
     sig = {
         "wn_create": (_p, [_u32, _u32, _u64]),
         "wn_create_streams": (_p, [_u32, _p, _p, _p, _u32, _p]),
@@ -78,6 +81,7 @@ def _load() -> ctypes.CDLL:
         "wn_get_pool": (_i, [_p, _u32, _p]),
         "wn_get_state": (_i, [_p, _u32, _p, _p, _p, _p, _p]),
         "wn_rng_draws": (_i, [_u64, _u64, _p]),
+        "wn_debug_report": (_i, [_p, _p, _i]),
         "wn_boxmuller": (_i, [_p, _u64, _u32, _u64, _i, _p]),
         "wn_save": (_i, [_p, _p, _u64, _p]),
         "wn_load": (_p, [_p, _u64, _p]),
@@ -104,7 +108,7 @@ def _L() -> ctypes.CDLL:
 def load() -> str:
     """Loads the CUDA library now (raises if it is missing); returns its path."""
     _L()
-    return _build.LIB
+    return library_path()
 
 _DTYPE_BYTES = {WN_F32: 4, WN_BF16: 2, WN_F16: 2}
 
@@ -361,6 +365,14 @@ def wn_rng_draws(seed: int, n: int) -> np.ndarray:
     out = np.zeros(n, dtype=np.uint64)
     _check(_L().wn_rng_draws(seed, n, out.ctypes.data), "wn_rng_draws")
     return out
+
+
+def wn_debug_report(reset: bool = False) -> tuple[int, int]:
+    """(violations, first) of the debug build's bounds record (raises WnError
+    on a library built without WN_DEBUG)."""
+    v, f = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(_L().wn_debug_report(ctypes.addressof(v), ctypes.addressof(f), int(bool(reset))), "wn_debug_report")
+    return v.value, f.value
 
 
 def wn_save(h: Handle) -> np.ndarray:

@@ -18,6 +18,10 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libwallace_gb300.so")
+# the debug build: device bounds checks (-DWN_DEBUG), relocatable device code
+# so that every translation unit counts into one violation record
+OUT_DIR_DEBUG = os.path.join(PKG, "_lib_debug")
+LIB_DEBUG = os.path.join(OUT_DIR_DEBUG, "libwallace_gb300_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
@@ -39,24 +43,26 @@ def _deps():
             glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps() + [__file__])
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    """Compile the library if any source is newer than it; returns its path."""
-    if not force and up_to_date():
-        return LIB
+def build(force: bool = False, verbose: bool = False, extra_flags=None, debug: bool = False) -> str:
+    """Compile the library if any source is newer than it; returns its path.
+    debug=True builds the bounds-checking library (LIB_DEBUG) instead."""
+    lib, out_dir = (LIB_DEBUG, OUT_DIR_DEBUG) if debug else (LIB, OUT_DIR)
+    if not force and up_to_date(lib):
+        return lib
     nvcc = _nvcc()
-    os.makedirs(OUT_DIR, exist_ok=True)
-    flags = NVCC_FLAGS + list(extra_flags or [])
+    os.makedirs(out_dir, exist_ok=True)
+    flags = NVCC_FLAGS + list(extra_flags or []) + (["-DWN_DEBUG", "-rdc=true"] if debug else [])
     objs = []
     cmds = []
     for src in _sources():
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         cmds.append([nvcc] + ARCH + flags + ["-c", src, "-o", obj])
 
@@ -71,12 +77,12 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     if verbose:
         for log in logs:
             print(log)
-    tmp = LIB + f".tmp{os.getpid()}"
-    run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs)
-    os.replace(tmp, LIB)
-    return LIB
+    tmp = lib + f".tmp{os.getpid()}"
+    run([nvcc] + ARCH + (["-rdc=true"] if debug else []) + ["-shared", "-o", tmp] + objs)
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -21,8 +21,12 @@ cudaError_t launch_gbm(const GenArgs &a, const GbmArgs &g, const LaunchCfg &c, b
 {
     switch (c.qt) {
     case 1: return launch_gbm_shape<1, 1024, 1>(a, g, c.threads, full, smem, cs);
+#ifndef WN_DEBUG
     case 4: return launch_gbm_shape<4, 288, 3>(a, g, c.threads, full, smem, cs);
+#endif
+#ifndef WN_DEBUG
     case 8: return launch_gbm_shape<8, 544, 1>(a, g, c.threads, full, smem, cs);
+#endif
     default: return cudaErrorInvalidValue;
     }
 }

@@ -20,6 +20,11 @@
 
 namespace wn {
 
+#ifdef WN_DEBUG
+// The debug build's violation record (wn_device.cuh, dbg_fail).
+__device__ unsigned long long wn_dbg_record[4];
+#endif
+
 // ---------------------------------------------------------------------------
 // Initialisation (Section 5.8): seed, N draws -> v_i = 2 (sum of the four
 // 16-bit fields) - 4*65535, scale so that sum v_i^2 = N.  The v_i and their
@@ -1852,6 +1857,27 @@ wn_status wn_get_state(const wn_stream *s, uint32_t i, uint64_t *host_xw, double
     if (host_k) *host_k = h.k;
     if (host_blocks) *host_blocks = h.blocks;
     return WN_OK;
+}
+
+wn_status wn_debug_report(uint64_t *host_violations, uint64_t *host_first, int reset)
+{
+#ifdef WN_DEBUG
+    unsigned long long rec[4] = {0, 0, 0, 0};
+    WN_CU(cudaDeviceSynchronize());
+    WN_CU(cudaMemcpyFromSymbol(rec, wn::wn_dbg_record, sizeof rec));
+    if (host_violations) *host_violations = rec[0];
+    if (host_first) *host_first = rec[1];
+    if (reset) {
+        const unsigned long long zero[4] = {0, 0, 0, 0};
+        WN_CU(cudaMemcpyToSymbol(wn::wn_dbg_record, zero, sizeof zero));
+    }
+    return WN_OK;
+#else
+    (void)reset;
+    if (host_violations) *host_violations = 0;
+    if (host_first) *host_first = 0;
+    return fail(WN_EINVAL, "wn_debug_report: this library was built without WN_DEBUG (no bounds checks)");
+#endif
 }
 
 wn_status wn_rng_draws(uint64_t seed, uint64_t n, uint64_t *host_out)

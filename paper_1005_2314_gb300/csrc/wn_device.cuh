@@ -79,6 +79,55 @@ __device__ __forceinline__ void seed_gen(uint64_t seed, uint64_t &x, uint64_t &w
     w = splitmix64(sm);
 }
 
+// --- the debug build (-DWN_DEBUG) -------------------------------------------
+// Device bounds checks that never trap: every checked access that would fall
+// outside its range (or be misaligned) is counted in wn_dbg_record, the first
+// one's kind and address kept, and skipped.  wn_dbg_record[0]: violations;
+// [1]: (kind << 56) | address of the first (kind 1: shared window address, 2:
+// global address).  The debug build compiles with relocatable device code, so
+// that every translation unit counts into the one record.
+#ifdef WN_DEBUG
+extern __device__ unsigned long long wn_dbg_record[4];
+__device__ __forceinline__ void dbg_fail(unsigned long long kind, unsigned long long where)
+{
+    if (atomicAdd(&wn_dbg_record[0], 1ull) == 0ull)
+        atomicExch(&wn_dbg_record[1], (kind << 56) | (where & 0x00FFFFFFFFFFFFFFull));
+}
+// The bytes [lo, hi) a stream's output may take.
+struct DbgRange {
+    const void *lo, *hi;
+};
+#else
+struct DbgRange {};
+#endif
+__device__ __forceinline__ DbgRange dbg_range(const void *lo, const void *hi)
+{
+#ifdef WN_DEBUG
+    return DbgRange{lo, hi};
+#else
+    (void)lo;
+    (void)hi;
+    return DbgRange{};
+#endif
+}
+// A global store of `bytes` at p: inside the range and aligned to `bytes`.
+__device__ __forceinline__ bool dbg_global_ok(const DbgRange &rg, const void *p, unsigned bytes)
+{
+#ifdef WN_DEBUG
+    const char *c = static_cast<const char *>(p);
+    if (c < static_cast<const char *>(rg.lo) || c + bytes > static_cast<const char *>(rg.hi) ||
+        reinterpret_cast<uintptr_t>(p) % bytes != 0) {
+        dbg_fail(2, reinterpret_cast<uintptr_t>(p));
+        return false;
+    }
+#else
+    (void)rg;
+    (void)p;
+    (void)bytes;
+#endif
+    return true;
+}
+
 template <typename T> __device__ __forceinline__ T to_out(float v);
 template <> __device__ __forceinline__ float to_out<float>(float v) { return v; }
 template <> __device__ __forceinline__ __nv_bfloat16 to_out<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }

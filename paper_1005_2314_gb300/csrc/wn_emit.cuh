@@ -161,7 +161,8 @@ __device__ __forceinline__ void run_stream_emit(StreamHdr *__restrict__ h, float
         ctl->gw = h->w;
     }
     __syncthreads();
-    for (uint64_t i = tid; i < n0; i += nthr) out[i] = to_out<OutT>(sc_prev * lds(ebuf(1) + 4u * (uint32_t)(k0 + i)));
+    const DbgRange rg = dbg_range(out, out + count);  // this stream's output (the debug build checks stores)
+    for (uint64_t i = tid; i < n0; i += nthr) store1(rg, out + i, sc_prev * lds(ebuf(1) + 4u * (uint32_t)(k0 + i)));
     __syncthreads();  // E[1] is read: block 1's final pass may overwrite it
 
     if (warp == 0) {
@@ -222,7 +223,7 @@ __device__ __forceinline__ void run_stream_emit(StreamHdr *__restrict__ h, float
 #pragma unroll
                 for (int u = 0; u < CH; ++u) {
                     const uint32_t i = c + lane + 32u * u;
-                    if (i < n_out) ob[i] = to_out<OutT>(sc_b * v[u]);
+                    if (i < n_out) store1(rg, ob + i, sc_b * v[u]);
                 }
             }
             ob += N - 1;
@@ -372,12 +373,18 @@ cudaError_t launch_emit_t(const GenArgs &a, const LaunchCfg &c, bool full, size_
                           : launch_emit_shape<1, 576, OutT>(a, c.threads, full, smem, cs);
     case 2: return narrow ? launch_emit_shape<2, 192, OutT>(a, c.threads, full, smem, cs)
                           : launch_emit_shape<2, 576, OutT>(a, c.threads, full, smem, cs);
+#ifndef WN_DEBUG
     case 4: return narrow ? launch_emit_shape<4, 192, OutT>(a, c.threads, full, smem, cs)
                           : launch_emit_shape<4, 576, OutT>(a, c.threads, full, smem, cs);
+#endif
+#ifndef WN_DEBUG
     case 8: return narrow ? launch_emit_shape<8, 192, OutT>(a, c.threads, full, smem, cs)
                           : launch_emit_shape<8, 576, OutT>(a, c.threads, full, smem, cs);
+#endif
+#ifndef WN_DEBUG
     case 16: return narrow ? launch_emit_shape<16, 192, OutT>(a, c.threads, full, smem, cs)
                            : launch_emit_shape<16, 576, OutT>(a, c.threads, full, smem, cs);
+#endif
     default: return cudaErrorInvalidValue;
     }
 }
@@ -390,9 +397,15 @@ cudaError_t launch_persist_emit_t(const GenArgs &a, const BatchArgs &bq, const L
     switch (c.qt) {
     case 1: return launch_persist_emit_shape<1, 192, OutT>(a, bq, c.threads, full, smem, sms, cs);
     case 2: return launch_persist_emit_shape<2, 192, OutT>(a, bq, c.threads, full, smem, sms, cs);
+#ifndef WN_DEBUG
     case 4: return launch_persist_emit_shape<4, 192, OutT>(a, bq, c.threads, full, smem, sms, cs);
+#endif
+#ifndef WN_DEBUG
     case 8: return launch_persist_emit_shape<8, 192, OutT>(a, bq, c.threads, full, smem, sms, cs);
+#endif
+#ifndef WN_DEBUG
     case 16: return launch_persist_emit_shape<16, 192, OutT>(a, bq, c.threads, full, smem, sms, cs);
+#endif
     default: return cudaErrorInvalidValue;
     }
 }

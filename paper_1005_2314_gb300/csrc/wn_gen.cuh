@@ -139,33 +139,60 @@ __host__ __device__ inline size_t gen_smem_bytes_ip(uint32_t n_max, uint32_t r_m
 extern __shared__ __align__(16) unsigned char wn_smem[];
 __device__ __forceinline__ uint32_t smem_base() { return (uint32_t)__cvta_generic_to_shared(wn_smem); }
 
+// The debug build checks every pool access against the CTA's dynamic shared
+// memory (window address and alignment; see DbgRange).
+__device__ __forceinline__ bool dbg_shared_ok(uint32_t a, uint32_t bytes)
+{
+#ifdef WN_DEBUG
+    uint32_t dyn;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    const uint32_t base = smem_base();
+    if (a < base || a + bytes > base + dyn || a % bytes != 0) {
+        dbg_fail(1, a);
+        return false;
+    }
+#else
+    (void)a;
+    (void)bytes;
+#endif
+    return true;
+}
+
 // Pool accesses by shared-window address.  ptxas orders ld/st.shared against
 // bar.sync itself, and the volatile asm keeps the compiler from moving them
 // across __syncthreads().
 __device__ __forceinline__ float lds(uint32_t a)
 {
+    if (!dbg_shared_ok(a, 4)) return 0.f;
     float v;
     asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
     return v;
 }
 __device__ __forceinline__ float4 lds4(uint32_t a)
 {
+    if (!dbg_shared_ok(a, 16)) return make_float4(0.f, 0.f, 0.f, 0.f);
     float4 v;
     asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
     return v;
 }
 __device__ __forceinline__ uint4 lds4u(uint32_t a)
 {
+    if (!dbg_shared_ok(a, 16)) return make_uint4(0u, 0u, 0u, 0u);
     uint4 v;
     asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
     return v;
 }
 __device__ __forceinline__ void sts4(uint32_t a, float2 lo, float2 hi)
 {
+    if (!dbg_shared_ok(a, 16)) return;
     asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(lo.x), "f"(lo.y), "f"(hi.x), "f"(hi.y));
 }
 
-__device__ __forceinline__ void sts1(uint32_t a, float v) { asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v)); }
+__device__ __forceinline__ void sts1(uint32_t a, float v)
+{
+    if (!dbg_shared_ok(a, 4)) return;
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v));
+}
 
 // Named barriers of the latency mode (0 is __syncthreads): the compute warps
 // end each pass on kBarPass among themselves; once per block the two control
@@ -260,23 +287,29 @@ __device__ __forceinline__ void make_tables(CtlState *ctl, PassTab *tab, uint32_
     }
 }
 
-template <typename OutT> __device__ __forceinline__ void store1(OutT *p, float v) { *p = to_out<OutT>(v); }
+template <typename OutT> __device__ __forceinline__ void store1(const DbgRange &rg, OutT *p, float v)
+{
+    if (dbg_global_ok(rg, p, sizeof(OutT))) *p = to_out<OutT>(v);
+}
 
 // Four consecutive values to an address aligned to four elements.
-__device__ __forceinline__ void store4(float *p, float a, float b, float c, float d)
+__device__ __forceinline__ void store4(const DbgRange &rg, float *p, float a, float b, float c, float d)
 {
+    if (!dbg_global_ok(rg, p, 16)) return;
     *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
 }
-__device__ __forceinline__ void store4(__nv_bfloat16 *p, float a, float b, float c, float d)
+__device__ __forceinline__ void store4(const DbgRange &rg, __nv_bfloat16 *p, float a, float b, float c, float d)
 {
+    if (!dbg_global_ok(rg, p, 8)) return;
     __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
     uint2 u;
     u.x = *reinterpret_cast<uint32_t *>(&lo);
     u.y = *reinterpret_cast<uint32_t *>(&hi);
     *reinterpret_cast<uint2 *>(p) = u;
 }
-__device__ __forceinline__ void store4(__half *p, float a, float b, float c, float d)
+__device__ __forceinline__ void store4(const DbgRange &rg, __half *p, float a, float b, float c, float d)
 {
+    if (!dbg_global_ok(rg, p, 8)) return;
     __half2 lo = __floats2half2_rn(a, b), hi = __floats2half2_rn(c, d);
     uint2 u;
     u.x = *reinterpret_cast<uint32_t *>(&lo);
@@ -339,7 +372,8 @@ template <int QT, bool FINAL, bool FULL, int EMIT, int A, typename OutT, bool RO
 __device__ __forceinline__ void pass_quads(uint32_t rd, uint32_t wr, uint32_t tab, uint32_t q0, uint32_t lane,
                                            uint32_t m4, uint32_t half, uint32_t nq, float2 &part, int nsync,
                                            OutT *__restrict__ ob, const float *sc_ptr, uint32_t n,
-                                           float2 (&acc)[QT][2], uint32_t rsv = 0, uint32_t nthr = 0)
+                                           float2 (&acc)[QT][2], uint32_t rsv = 0, uint32_t nthr = 0,
+                                           const DbgRange &rg = DbgRange{})
 {
     static_assert(!(HAND && IP), "the latency mode keeps two pool buffers");
     const uint4 P = lds4u(tab);
@@ -418,10 +452,10 @@ __device__ __forceinline__ void pass_quads(uint32_t rd, uint32_t wr, uint32_t ta
         const uint32_t pos = 4u * q;
         if (EMIT == EMIT_PART) {
             if (act) {
-                if (pos < n) store1(ob + pos, v01.x);
-                if (pos + 1 < n) store1(ob + pos + 1, v01.y);
-                if (pos + 2 < n) store1(ob + pos + 2, v23.x);
-                if (pos + 3 < n) store1(ob + pos + 3, v23.y);
+                if (pos < n) store1(rg, ob + pos, v01.x);
+                if (pos + 1 < n) store1(rg, ob + pos + 1, v01.y);
+                if (pos + 2 < n) store1(rg, ob + pos + 2, v23.x);
+                if (pos + 3 < n) store1(rg, ob + pos + 3, v23.y);
             }
             continue;
         }
@@ -437,28 +471,28 @@ __device__ __forceinline__ void pass_quads(uint32_t rd, uint32_t wr, uint32_t ta
         // only be the last j)
         const bool last = (FULL && j != QT - 1) ? false : (q + 1u == nq);
         if (A == 0) {
-            if (!last) store4(ob + pos, v01.x, v01.y, v23.x, v23.y);
+            if (!last) store4(rg, ob + pos, v01.x, v01.y, v23.x, v23.y);
             else {
-                store1(ob + pos, v01.x);
-                store1(ob + pos + 1, v01.y);
-                store1(ob + pos + 2, v23.x);
+                store1(rg, ob + pos, v01.x);
+                store1(rg, ob + pos + 1, v01.y);
+                store1(rg, ob + pos + 2, v23.x);
             }
             continue;
         }
         if (j == 0 && lane == 0) {  // predecessor in another warp: own first 4 - A only
-            store1(ob + pos, v01.x);
-            if (A <= 2) store1(ob + pos + 1, v01.y);
-            if (A == 1) store1(ob + pos + 2, v23.x);
+            store1(rg, ob + pos, v01.x);
+            if (A <= 2) store1(rg, ob + pos + 1, v01.y);
+            if (A == 1) store1(rg, ob + pos + 2, v23.x);
         } else {
             OutT *g = ob + (pos - A);
-            if (A == 1) store4(g, p3, v01.x, v01.y, v23.x);
-            else if (A == 2) store4(g, p2, p3, v01.x, v01.y);
-            else store4(g, p1, p2, p3, v01.x);
+            if (A == 1) store4(rg, g, p3, v01.x, v01.y, v23.x);
+            else if (A == 2) store4(rg, g, p2, p3, v01.x, v01.y);
+            else store4(rg, g, p1, p2, p3, v01.x);
         }
         if ((j == QT - 1 && l31) || last) {  // successor cannot take the last A
-            if (A == 3) store1(ob + pos + 1, v01.y);
-            if (A >= 2) store1(ob + pos + 2, v23.x);
-            if (!last) store1(ob + pos + 3, v23.y);
+            if (A == 3) store1(rg, ob + pos + 1, v01.y);
+            if (A >= 2) store1(rg, ob + pos + 2, v23.x);
+            if (!last) store1(rg, ob + pos + 3, v23.y);
         }
     }
 }
@@ -502,6 +536,7 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
     CtlState *ctl = reinterpret_cast<CtlState *>(smem + 256);
     PassTab *tabs = reinterpret_cast<PassTab *>(smem + 256 + sizeof(CtlState));  // [2][r_max]
     const uint32_t tabs_s = base + 256u + (uint32_t)sizeof(CtlState);
+    const DbgRange rg = dbg_range(out, out + count);  // this stream's output (the debug build checks stores)
     // bytes per buffer; buffer i at window W0 + i bsz (in place: one buffer)
     const uint32_t bsz = IP ? 0u : 4u * n_max;
     const uint32_t nwc = (blockDim.x >> 5) - 1u;  // compute warps
@@ -543,7 +578,7 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
     __syncthreads();
     if (store)
         for (uint64_t i = tid; i < n0; i += blockDim.x)
-            out[i] = to_out<OutT>(sc_prev * lds(W0 + 4u * (uint32_t)(k0 + i)));
+            store1(rg, out + i, sc_prev * lds(W0 + 4u * (uint32_t)(k0 + i)));
     if (IP && store && n0 > 0) __syncthreads();  // the control warp's reads precede the first pass's stores
 
     // Control warp: FP64 sum of the compute warps' partial sums of squares of
@@ -621,32 +656,32 @@ __device__ __forceinline__ void run_stream(StreamHdr *__restrict__ h, float *__r
                 const bool whole = ((dec == 1 ? b : e) + 1 < nb) || tail == 0;
                 if (GBM && emit) {
                     pass_quads<QT, true, FULL, EMIT_GBM, 0, OutT, ROT, false, IP>(
-                        rd, wr, tp, q0, lane, m4, half, nq, part, nsync, ob, scp, 0, acc, rsv, ncomp);
+                        rd, wr, tp, q0, lane, m4, half, nq, part, nsync, ob, scp, 0, acc, rsv, ncomp, rg);
                 } else if (!store || !emit) {
                     pass_quads<QT, true, FULL, EMIT_NONE, 0, OutT, ROT, false, IP>(
-                        rd, wr, tp, q0, lane, m4, half, nq, part, 0, ob, scp, 0, acc, rsv, ncomp);
+                        rd, wr, tp, q0, lane, m4, half, nq, part, 0, ob, scp, 0, acc, rsv, ncomp, rg);
                     if (nsync > 0) __syncthreads();
                     if (nsync > 1) __syncthreads();
                 } else if (!whole) {
                     pass_quads<QT, true, FULL, EMIT_PART, 0, OutT, ROT, false, IP>(
-                        rd, wr, tp, q0, lane, m4, half, nq, part, nsync, ob, scp, (uint32_t)tail, acc, rsv, ncomp);
+                        rd, wr, tp, q0, lane, m4, half, nq, part, nsync, ob, scp, (uint32_t)tail, acc, rsv, ncomp, rg);
                 } else {
                     switch (a) {
                     case 0:
                         pass_quads<QT, true, FULL, EMIT_WHOLE, 0, OutT, ROT, false, IP>(
-                            rd, wr, tp, q0, lane, m4, half, nq, part, nsync, ob, scp, 0, acc, rsv, ncomp);
+                            rd, wr, tp, q0, lane, m4, half, nq, part, nsync, ob, scp, 0, acc, rsv, ncomp, rg);
                         break;
                     case 1:
                         pass_quads<QT, true, FULL, EMIT_WHOLE, 1, OutT, ROT, false, IP>(
-                            rd, wr, tp, q0, lane, m4, half, nq, part, nsync, ob, scp, 0, acc, rsv, ncomp);
+                            rd, wr, tp, q0, lane, m4, half, nq, part, nsync, ob, scp, 0, acc, rsv, ncomp, rg);
                         break;
                     case 2:
                         pass_quads<QT, true, FULL, EMIT_WHOLE, 2, OutT, ROT, false, IP>(
-                            rd, wr, tp, q0, lane, m4, half, nq, part, nsync, ob, scp, 0, acc, rsv, ncomp);
+                            rd, wr, tp, q0, lane, m4, half, nq, part, nsync, ob, scp, 0, acc, rsv, ncomp, rg);
                         break;
                     default:
                         pass_quads<QT, true, FULL, EMIT_WHOLE, 3, OutT, ROT, false, IP>(
-                            rd, wr, tp, q0, lane, m4, half, nq, part, nsync, ob, scp, 0, acc, rsv, ncomp);
+                            rd, wr, tp, q0, lane, m4, half, nq, part, nsync, ob, scp, 0, acc, rsv, ncomp, rg);
                         break;
                     }
                 }
@@ -738,6 +773,7 @@ __device__ __forceinline__ void run_stream_lat(StreamHdr *__restrict__ h, float 
         return;
     }
     float *red = reinterpret_cast<float *>(smem);  // [2][32] partial sums by block parity; [par][31]: slot N-1
+    const DbgRange rg = dbg_range(out, out + count);
     CtlState *ctl = reinterpret_cast<CtlState *>(smem + 256);
     PassTab *tabs = reinterpret_cast<PassTab *>(smem + 256 + sizeof(CtlState));  // [2][r_max]
     const uint32_t tabs_s = base + 256u + (uint32_t)sizeof(CtlState);
@@ -769,8 +805,7 @@ __device__ __forceinline__ void run_stream_lat(StreamHdr *__restrict__ h, float 
     }
     __syncthreads();
     if (warp == 1 && nb > 0) make_tables(ctl, tabs, R, N, lane, false);
-    for (uint64_t i = tid; i < n0; i += blockDim.x)
-        out[i] = to_out<OutT>(sc_prev * lds(W0 + 4u * (uint32_t)(k0 + i)));
+    for (uint64_t i = tid; i < n0; i += blockDim.x) store1(rg, out + i, sc_prev * lds(W0 + 4u * (uint32_t)(k0 + i)));
     __syncthreads();  // block 0's tables are there and buffer 0 has been read
 
     uint32_t cb = (uint32_t)((nb * R) & 1u);  // the control warps only need the final buffer
@@ -824,24 +859,24 @@ __device__ __forceinline__ void run_stream_lat(StreamHdr *__restrict__ h, float 
                     const bool whole = (b + 1 < nb) || tail == 0;
                     if (!whole) {
                         pass_quads<QT, true, FULL, EMIT_PART, 0, OutT, false, true>(
-                            rd, wr, tp, q0, lane, m4, half, nq, part, 0, ob, scp, (uint32_t)tail, acc, rsv, nthr);
+                            rd, wr, tp, q0, lane, m4, half, nq, part, 0, ob, scp, (uint32_t)tail, acc, rsv, nthr, rg);
                     } else {
                         switch (a) {
                         case 0:
                             pass_quads<QT, true, FULL, EMIT_WHOLE, 0, OutT, false, true>(
-                                rd, wr, tp, q0, lane, m4, half, nq, part, 0, ob, scp, 0, acc, rsv, nthr);
+                                rd, wr, tp, q0, lane, m4, half, nq, part, 0, ob, scp, 0, acc, rsv, nthr, rg);
                             break;
                         case 1:
                             pass_quads<QT, true, FULL, EMIT_WHOLE, 1, OutT, false, true>(
-                                rd, wr, tp, q0, lane, m4, half, nq, part, 0, ob, scp, 0, acc, rsv, nthr);
+                                rd, wr, tp, q0, lane, m4, half, nq, part, 0, ob, scp, 0, acc, rsv, nthr, rg);
                             break;
                         case 2:
                             pass_quads<QT, true, FULL, EMIT_WHOLE, 2, OutT, false, true>(
-                                rd, wr, tp, q0, lane, m4, half, nq, part, 0, ob, scp, 0, acc, rsv, nthr);
+                                rd, wr, tp, q0, lane, m4, half, nq, part, 0, ob, scp, 0, acc, rsv, nthr, rg);
                             break;
                         default:
                             pass_quads<QT, true, FULL, EMIT_WHOLE, 3, OutT, false, true>(
-                                rd, wr, tp, q0, lane, m4, half, nq, part, 0, ob, scp, 0, acc, rsv, nthr);
+                                rd, wr, tp, q0, lane, m4, half, nq, part, 0, ob, scp, 0, acc, rsv, nthr, rg);
                             break;
                         }
                     }
@@ -997,13 +1032,23 @@ cudaError_t launch_persist_t(const GenArgs &a, const BatchArgs &bq, const Launch
     case shape_key(1, 1024, 0):
         return launch_persist_shape<1, 1024, 1, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
     case shape_key(2, 544, 0): return launch_persist_shape<2, 544, 2, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
+#ifndef WN_DEBUG
     case shape_key(4, 288, 0): return launch_persist_shape<4, 288, 4, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
+#endif
+#ifndef WN_DEBUG
     case shape_key(8, 160, 0): return launch_persist_shape<8, 160, 4, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
+#endif
+#ifndef WN_DEBUG
     case shape_key(8, 544, 0): return launch_persist_shape<8, 544, 1, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
+#endif
+#ifndef WN_DEBUG
     case shape_key(16, 288, 0):
         return launch_persist_shape<16, 288, 1, OutT>(a, bq, c.threads, full, var, smem, sms, cs);
+#endif
+#ifndef WN_DEBUG
     case shape_key(16, 288, 1):
         return launch_persist_shape<16, 288, 2, OutT, true>(a, bq, c.threads, full, var, smem, sms, cs);
+#endif
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1046,11 +1091,21 @@ cudaError_t launch_generate_t(const GenArgs &a, const LaunchCfg &c, bool full, b
     switch (shape_key(c.qt, c.maxt, c.ip)) {
     case shape_key(1, 1024, 0): return launch_shape<1, 1024, 1, OutT>(a, c.threads, full, var, smem, cs);
     case shape_key(2, 544, 0): return launch_shape<2, 544, 2, OutT>(a, c.threads, full, var, smem, cs);
+#ifndef WN_DEBUG
     case shape_key(4, 288, 0): return launch_shape<4, 288, 4, OutT>(a, c.threads, full, var, smem, cs);
+#endif
+#ifndef WN_DEBUG
     case shape_key(8, 160, 0): return launch_shape<8, 160, 4, OutT>(a, c.threads, full, var, smem, cs);
+#endif
+#ifndef WN_DEBUG
     case shape_key(8, 544, 0): return launch_shape<8, 544, 1, OutT>(a, c.threads, full, var, smem, cs);
+#endif
+#ifndef WN_DEBUG
     case shape_key(16, 288, 0): return launch_shape<16, 288, 1, OutT>(a, c.threads, full, var, smem, cs);
+#endif
+#ifndef WN_DEBUG
     case shape_key(16, 288, 1): return launch_shape<16, 288, 2, OutT, true>(a, c.threads, full, var, smem, cs);
+#endif
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1114,10 +1169,18 @@ cudaError_t launch_persist_lat_t(const GenArgs &a, const BatchArgs &bq, const La
     switch (c.qt * 10000 + c.maxt) {
     case 1 * 10000 + 1024: return launch_persist_lat_shape<1, 1024, 1, OutT>(a, bq, c.threads, full, smem, sms, cs);
     case 2 * 10000 + 544: return launch_persist_lat_shape<2, 544, 2, OutT>(a, bq, c.threads, full, smem, sms, cs);
+#ifndef WN_DEBUG
     case 4 * 10000 + 288: return launch_persist_lat_shape<4, 288, 4, OutT>(a, bq, c.threads, full, smem, sms, cs);
+#endif
+#ifndef WN_DEBUG
     case 8 * 10000 + 160: return launch_persist_lat_shape<8, 160, 4, OutT>(a, bq, c.threads, full, smem, sms, cs);
+#endif
+#ifndef WN_DEBUG
     case 8 * 10000 + 544: return launch_persist_lat_shape<8, 544, 1, OutT>(a, bq, c.threads, full, smem, sms, cs);
+#endif
+#ifndef WN_DEBUG
     case 16 * 10000 + 288: return launch_persist_lat_shape<16, 288, 1, OutT>(a, bq, c.threads, full, smem, sms, cs);
+#endif
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1138,10 +1201,18 @@ cudaError_t launch_latency_t(const GenArgs &a, const LaunchCfg &c, bool full, si
     switch (c.qt * 10000 + c.maxt) {
     case 1 * 10000 + 1024: return launch_latency_shape<1, 1024, 1, OutT>(a, c.threads, full, smem, cs);
     case 2 * 10000 + 544: return launch_latency_shape<2, 544, 2, OutT>(a, c.threads, full, smem, cs);
+#ifndef WN_DEBUG
     case 4 * 10000 + 288: return launch_latency_shape<4, 288, 4, OutT>(a, c.threads, full, smem, cs);
+#endif
+#ifndef WN_DEBUG
     case 8 * 10000 + 160: return launch_latency_shape<8, 160, 4, OutT>(a, c.threads, full, smem, cs);
+#endif
+#ifndef WN_DEBUG
     case 8 * 10000 + 544: return launch_latency_shape<8, 544, 1, OutT>(a, c.threads, full, smem, cs);
+#endif
+#ifndef WN_DEBUG
     case 16 * 10000 + 288: return launch_latency_shape<16, 288, 1, OutT>(a, c.threads, full, smem, cs);
+#endif
     default: return cudaErrorInvalidValue;
     }
 }

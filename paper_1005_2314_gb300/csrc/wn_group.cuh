@@ -42,12 +42,14 @@ __host__ __device__ inline size_t group_smem_bytes(uint32_t N) { return kGroupSm
 // Pool accesses at offset o (bytes) from the pool buffer.
 __device__ __forceinline__ float gld(uint32_t o)
 {
+    if (!dbg_shared_ok(o + kGroupPool, 4)) return 0.f;
     float v;
     asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(o), "n"(kGroupPool));
     return v;
 }
 __device__ __forceinline__ float4 gld4(uint32_t o)
 {
+    if (!dbg_shared_ok(o + kGroupPool, 16)) return make_float4(0.f, 0.f, 0.f, 0.f);
     float4 v;
     asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4+%5];"
                  : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
@@ -56,6 +58,7 @@ __device__ __forceinline__ float4 gld4(uint32_t o)
 }
 __device__ __forceinline__ void gst4(uint32_t o, float2 lo, float2 hi)
 {
+    if (!dbg_shared_ok(o + kGroupPool, 16)) return;
     asm volatile("st.shared.v4.f32 [%0+%5], {%1, %2, %3, %4};" ::"r"(o), "f"(lo.x), "f"(lo.y), "f"(hi.x), "f"(hi.y),
                  "n"(kGroupPool));
 }
@@ -126,7 +129,7 @@ __device__ __forceinline__ float group_scale_f32(float ss, float r, float A, flo
 // reserved value and never written).
 template <int QT, int A, bool PART, typename OutT>
 __device__ __forceinline__ void group_emit(OutT *__restrict__ ob, const float2 (&y)[QT][2], float sc, uint32_t q0,
-                                           uint32_t lane, uint32_t nq, uint32_t n)
+                                           uint32_t lane, uint32_t nq, uint32_t n, const DbgRange &rg)
 {
     const float2 sc2 = make_float2(sc, sc);
     const uint32_t src = (lane + 31u) & 31u;
@@ -138,10 +141,10 @@ __device__ __forceinline__ void group_emit(OutT *__restrict__ ob, const float2 (
         const float2 v01 = fmul2(y[j][0], sc2), v23 = fmul2(y[j][1], sc2);
         const uint32_t pos = 4u * q;
         if (PART) {
-            if (pos < n) store1(ob + pos, v01.x);
-            if (pos + 1 < n) store1(ob + pos + 1, v01.y);
-            if (pos + 2 < n) store1(ob + pos + 2, v23.x);
-            if (pos + 3 < n) store1(ob + pos + 3, v23.y);
+            if (pos < n) store1(rg, ob + pos, v01.x);
+            if (pos + 1 < n) store1(rg, ob + pos + 1, v01.y);
+            if (pos + 2 < n) store1(rg, ob + pos + 2, v23.x);
+            if (pos + 3 < n) store1(rg, ob + pos + 3, v23.y);
             continue;
         }
         float p1 = 0.f, p2 = 0.f, p3 = 0.f;
@@ -153,28 +156,28 @@ __device__ __forceinline__ void group_emit(OutT *__restrict__ ob, const float2 (
         l3 = v23.y;
         const bool last = (j == QT - 1) && (q + 1u == nq);  // the quadruple holding the reserved slot
         if (A == 0) {
-            if (!last) store4(ob + pos, v01.x, v01.y, v23.x, v23.y);
+            if (!last) store4(rg, ob + pos, v01.x, v01.y, v23.x, v23.y);
             else {
-                store1(ob + pos, v01.x);
-                store1(ob + pos + 1, v01.y);
-                store1(ob + pos + 2, v23.x);
+                store1(rg, ob + pos, v01.x);
+                store1(rg, ob + pos + 1, v01.y);
+                store1(rg, ob + pos + 2, v23.x);
             }
             continue;
         }
         if (j == 0 && lane == 0) {  // predecessor in another warp (or before the block): own first 4 - A
-            store1(ob + pos, v01.x);
-            if (A <= 2) store1(ob + pos + 1, v01.y);
-            if (A == 1) store1(ob + pos + 2, v23.x);
+            store1(rg, ob + pos, v01.x);
+            if (A <= 2) store1(rg, ob + pos + 1, v01.y);
+            if (A == 1) store1(rg, ob + pos + 2, v23.x);
         } else {
             OutT *g = ob + (pos - A);
-            if (A == 1) store4(g, p3, v01.x, v01.y, v23.x);
-            else if (A == 2) store4(g, p2, p3, v01.x, v01.y);
-            else store4(g, p1, p2, p3, v01.x);
+            if (A == 1) store4(rg, g, p3, v01.x, v01.y, v23.x);
+            else if (A == 2) store4(rg, g, p2, p3, v01.x, v01.y);
+            else store4(rg, g, p1, p2, p3, v01.x);
         }
         if ((j == QT - 1 && l31) || last) {  // successor cannot take the last A
-            if (A == 3) store1(ob + pos + 1, v01.y);
-            if (A >= 2) store1(ob + pos + 2, v23.x);
-            if (!last) store1(ob + pos + 3, v23.y);
+            if (A == 3) store1(rg, ob + pos + 1, v01.y);
+            if (A >= 2) store1(rg, ob + pos + 2, v23.x);
+            if (!last) store1(rg, ob + pos + 3, v23.y);
         }
     }
 }
@@ -189,6 +192,7 @@ __device__ __forceinline__ void run_stream_group(StreamHdr *__restrict__ h, floa
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t N = 128u * QT * G, nq = N / 4;
     float *red = reinterpret_cast<float *>(wn_smem);  // [2][G] partial sums by block parity; [2][8]: slot N-1
+    const DbgRange rg = dbg_range(out, out + count);   // this stream's output (the debug build checks stores)
     if (smem_base() != kGroupBase || h->N != N) {     // not the layout this kernel was built for
         if (tid == 0) h->flags |= 1u;
         return;
@@ -213,7 +217,7 @@ __device__ __forceinline__ void run_stream_group(StreamHdr *__restrict__ h, floa
     float sc = nb > 0 ? group_scale(h->sumsq, (float)h->r, A, B, N) : sc_prev;
     double ss = h->sumsq;
     group_sync<G>();
-    for (uint64_t i = tid; i < n0; i += 32u * G) out[i] = to_out<OutT>(sc_prev * gld(4u * (uint32_t)(k0 + i)));
+    for (uint64_t i = tid; i < n0; i += 32u * G) store1(rg, out + i, sc_prev * gld(4u * (uint32_t)(k0 + i)));
 
     const uint32_t q0 = warp * 32u * QT + lane;
     const uint32_t m4 = 4u * N - 1u, half = 2u * N;
@@ -253,13 +257,13 @@ __device__ __forceinline__ void run_stream_group(StreamHdr *__restrict__ h, floa
         // the block's values (scale sc), then the next block's scale
         const bool whole = (b + 1 < nb) || tail == 0;
         if (!whole) {
-            group_emit<QT, 0, true, OutT>(ob, y, sc, q0, lane, nq, (uint32_t)tail);
+            group_emit<QT, 0, true, OutT>(ob, y, sc, q0, lane, nq, (uint32_t)tail, rg);
         } else {
             switch (a) {
-            case 0: group_emit<QT, 0, false, OutT>(ob, y, sc, q0, lane, nq, 0); break;
-            case 1: group_emit<QT, 1, false, OutT>(ob, y, sc, q0, lane, nq, 0); break;
-            case 2: group_emit<QT, 2, false, OutT>(ob, y, sc, q0, lane, nq, 0); break;
-            default: group_emit<QT, 3, false, OutT>(ob, y, sc, q0, lane, nq, 0); break;
+            case 0: group_emit<QT, 0, false, OutT>(ob, y, sc, q0, lane, nq, 0, rg); break;
+            case 1: group_emit<QT, 1, false, OutT>(ob, y, sc, q0, lane, nq, 0, rg); break;
+            case 2: group_emit<QT, 2, false, OutT>(ob, y, sc, q0, lane, nq, 0, rg); break;
+            default: group_emit<QT, 3, false, OutT>(ob, y, sc, q0, lane, nq, 0, rg); break;
             }
         }
         float ps = part.x + part.y;
@@ -370,15 +374,33 @@ cudaError_t launch_group_t(const GenArgs &a, uint32_t N, uint32_t G, int sms, cu
 {
     switch (N * 16 + G) {
     case 1024 * 16 + 1: return launch_group_shape<1, 8, 16, OutT>(a, sms, cs, ctas_per_sm);
+#ifndef WN_DEBUG
     case 2048 * 16 + 1: return launch_group_shape<1, 16, 12, OutT>(a, sms, cs, ctas_per_sm);
+#endif
+#ifndef WN_DEBUG
     case 4096 * 16 + 1: return launch_group_shape<1, 32, 9, OutT>(a, sms, cs, ctas_per_sm);
+#endif
+#ifndef WN_DEBUG
     case 4096 * 16 + 2: return launch_group_shape<2, 16, 9, OutT>(a, sms, cs, ctas_per_sm);
+#endif
+#ifndef WN_DEBUG
     case 4096 * 16 + 4: return launch_group_shape<4, 8, 6, OutT>(a, sms, cs, ctas_per_sm);
+#endif
+#ifndef WN_DEBUG
     case 4096 * 16 + 8: return launch_group_shape<8, 4, 4, OutT>(a, sms, cs, ctas_per_sm);
+#endif
+#ifndef WN_DEBUG
     case 1024 * 16 + 4: return launch_group_shape<4, 2, 8, OutT>(a, sms, cs, ctas_per_sm);
+#endif
+#ifndef WN_DEBUG
     case 16384 * 16 + 8: return launch_group_shape<8, 16, 2, OutT>(a, sms, cs, ctas_per_sm);
+#endif
+#ifndef WN_DEBUG
     case 8192 * 16 + 2: return launch_group_shape<2, 32, 4, OutT>(a, sms, cs, ctas_per_sm);
+#endif
+#ifndef WN_DEBUG
     case 16384 * 16 + 4: return launch_group_shape<4, 32, 3, OutT>(a, sms, cs, ctas_per_sm);
+#endif
     default: return cudaErrorInvalidValue;
     }
 }
@@ -441,15 +463,33 @@ cudaError_t launch_persist_group_t(const GenArgs &a, const BatchArgs &bq, uint32
 {
     switch (N * 16 + G) {
     case 1024 * 16 + 1: return launch_persist_group_shape<1, 8, 16, OutT>(a, bq, sms, cs);
+#ifndef WN_DEBUG
     case 1024 * 16 + 4: return launch_persist_group_shape<4, 2, 8, OutT>(a, bq, sms, cs);
+#endif
+#ifndef WN_DEBUG
     case 2048 * 16 + 1: return launch_persist_group_shape<1, 16, 12, OutT>(a, bq, sms, cs);
+#endif
+#ifndef WN_DEBUG
     case 4096 * 16 + 1: return launch_persist_group_shape<1, 32, 9, OutT>(a, bq, sms, cs);
+#endif
+#ifndef WN_DEBUG
     case 4096 * 16 + 2: return launch_persist_group_shape<2, 16, 9, OutT>(a, bq, sms, cs);
+#endif
+#ifndef WN_DEBUG
     case 4096 * 16 + 4: return launch_persist_group_shape<4, 8, 6, OutT>(a, bq, sms, cs);
+#endif
+#ifndef WN_DEBUG
     case 4096 * 16 + 8: return launch_persist_group_shape<8, 4, 4, OutT>(a, bq, sms, cs);
+#endif
+#ifndef WN_DEBUG
     case 8192 * 16 + 2: return launch_persist_group_shape<2, 32, 4, OutT>(a, bq, sms, cs);
+#endif
+#ifndef WN_DEBUG
     case 16384 * 16 + 4: return launch_persist_group_shape<4, 32, 3, OutT>(a, bq, sms, cs);
+#endif
+#ifndef WN_DEBUG
     case 16384 * 16 + 8: return launch_persist_group_shape<8, 16, 2, OutT>(a, bq, sms, cs);
+#endif
     default: return cudaErrorInvalidValue;
     }
 }
