@@ -16,9 +16,9 @@
 //
 // Each block's scale (Section 5.5) is formed at the end of the block before
 // it, from that block's sum of squares (FP32 within a warp, FP64 across warps
-// and for its deviation from N) and its reserved value -- the sum of squares
-// when the block starts, which the orthogonal passes preserve exactly in
-// exact arithmetic.  The final pass stores the block's values straight from
+// and for its deviation from N, which for one warp's FP32 sum FP32 computes
+// exactly) and its reserved value -- the sum of squares when the block
+// starts, which the orthogonal passes preserve exactly in exact arithmetic.  The final pass stores the block's values straight from
 // registers as 16-byte (FP32) or 8-byte (16-bit) stores, realigned by warp
 // shuffles, as the ordinary kernel does.
 #pragma once
@@ -277,15 +277,22 @@ __device__ __forceinline__ void run_stream_group(StreamHdr *__restrict__ h, floa
             if (lane == 0) red[par * 8u + warp] = ps;
             if (warp == G - 1 && lane == 31) red[16u + par] = y[QT - 1][1].y;
             __syncthreads();  // partial sums published; also ends the pass
-            double t = 0.0;
+            double t4[G];  // the warps' partial sums, added pairwise in FP64
 #pragma unroll
-            for (int w = 0; w < G; ++w) t += (double)red[par * 8u + w];
-            ss = t;
+            for (int w = 0; w < G; ++w) t4[w] = (double)red[par * 8u + w];
+#pragma unroll
+            for (int st = 1; st < G; st <<= 1)
+#pragma unroll
+                for (int w = 0; w + st < G; w += 2 * st) t4[w] += t4[w + st];
+            ss = t4[0];
             rv = red[16u + par];
         }
         if (G == 1) __syncwarp();  // the final pass's stores precede the next block's gathers
         const float r = sc * rv;   // this block's reserved value, scaled (Section 5.5, fastnorm2)
-        if (b + 1 < nb) sc = group_scale(ss, r, A, B, N);
+        // one warp's sum is an FP32 value, for which the FP32 route gives the
+        // FP64 route's bits (group_scale_f32); several warps' partial sums are
+        // added in FP64 (pairwise) and take the FP64 route
+        if (b + 1 < nb) sc = (G == 1) ? group_scale_f32((float)ss, r, A, B, N) : group_scale(ss, r, A, B, N);
         ob += N - 1;
         a = (a + N - 1) & 3u;
     }
