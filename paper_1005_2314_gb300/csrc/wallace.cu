@@ -1630,19 +1630,30 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
         cands.push_back({third, 1});
         for (int dd : {2, 4})
             for (int k = 32; k <= dd * s->sms && k <= (int)s->n; k *= 2) cands.push_back({k, dd});
-        float best_ms = 1e30f;
-        for (const auto &cd : cands) {
-            const int k = cd.first;
+        // each plan also with every group that has a latency shape in the
+        // latency mode: the groups were timed without the estimate's chains,
+        // and the requests left in them are serial chains too
+        const std::map<uint32_t, bool> tuned_lat = s->group_lat;
+        std::map<uint32_t, bool> all_lat = tuned_lat;
+        for (const auto &g : groups) {
+            LaunchCfg lc;
+            if (!s->var && latency_default(g.N, lc)) all_lat[g.N] = true;
+        }
+        const size_t nplan = cands.size();
+        // median time of `reps` replays of the batch under plan ci (after one
+        // untimed); the groups' CTAs reach the SMs in a different order on
+        // every run, so single replays vary by ~10%
+        auto score = [&](size_t ci, int reps, float &t_ms) {
+            const auto &cd = cands[ci % nplan];
+            s->group_lat = ci >= nplan ? all_lat : tuned_lat;
             s->batch_density = cd.second;
             std::vector<uint32_t> ord;
-            const std::vector<Group> gk = plan_batch(s, counts, ord, k);
-            if (gk.size() > 16) continue;
-            if ((st = ensure_batch_buffers(s, gk.size())) != WN_OK) break;
+            const std::vector<Group> gk = plan_batch(s, counts, ord, cd.first);
+            if (gk.size() > 16) return false;
+            if ((st = ensure_batch_buffers(s, gk.size())) != WN_OK) return false;
             e = cudaMemcpyAsync(d.order, ord.data(), sizeof(uint32_t) * s->n, cudaMemcpyHostToDevice, cs);
-            // the groups' CTAs reach the SMs in a different order on every
-            // run, so a single replay varies by ~10%: score the median of four
-            float times[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int rep = 0; rep < 5 && e == cudaSuccess && st == WN_OK; ++rep) {
+            std::vector<float> times;
+            for (int rep = 0; rep <= reps && e == cudaSuccess && st == WN_OK; ++rep) {
                 e = restore();
                 if (e == cudaSuccess) e = cudaEventRecord(e0, cs);
                 if (e == cudaSuccess) st = enqueue_batch(s, gk, out, dtype, cs, d);
@@ -1650,16 +1661,31 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 float ms = 0.f;
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-                if (rep > 0) times[rep - 1] = ms;
+                if (rep > 0) times.push_back(ms);
             }
-            if (e != cudaSuccess || st != WN_OK) break;
-            std::sort(times, times + 4);
-            const float t_ms = 0.5f * (times[1] + times[2]);
-            if (t_ms < best_ms) {
-                best_ms = t_ms;
-                best_crit = k;
-                best_density = cd.second;
-            }
+            if (e != cudaSuccess || st != WN_OK || times.empty()) return false;
+            std::sort(times.begin(), times.end());
+            const size_t m = times.size();
+            t_ms = (m % 2) ? times[m / 2] : 0.5f * (times[m / 2 - 1] + times[m / 2]);
+            return true;
+        };
+        // every plan on four replays; then the best three again on eight, so
+        // that one lucky score does not decide
+        std::vector<std::pair<float, size_t>> scored;
+        for (size_t ci = 0; ci < 2 * nplan && e == cudaSuccess && st == WN_OK; ++ci) {
+            if (ci >= nplan && all_lat == tuned_lat) break;  // nothing different to try
+            float t = 0.f;
+            if (score(ci, 4, t)) scored.push_back({t, ci});
+        }
+        std::sort(scored.begin(), scored.end());
+        float best_ms = 1e30f;
+        for (size_t r = 0; r < scored.size() && r < 3 && e == cudaSuccess && st == WN_OK; ++r) {
+            float t = 0.f;
+            if (!score(scored[r].second, 8, t) || t >= best_ms) continue;
+            best_ms = t;
+            best_crit = cands[scored[r].second % nplan].first;
+            best_density = cands[scored[r].second % nplan].second;
+            for (auto &kv : s->group_lat) chosen_lat[kv.first] = kv.second;
         }
     }
     s->batch_density = old_density;
