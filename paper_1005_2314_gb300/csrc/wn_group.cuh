@@ -124,8 +124,9 @@ __device__ __forceinline__ float group_scale_f32(float ss, float r, float A, flo
 
 // The final pass's output: y (this thread's quadruples q0 + 32 j, unscaled)
 // times sc to ob[4q + k], as in the ordinary kernel's EMIT_WHOLE (A = element
-// offset of ob from a 16-byte boundary) or, with PART, the first n values
-// with single stores.  nq: quadruples of the pool (slot 4 nq - 1 is the
+// offset of ob from a 16-byte boundary; for A = 3 the aligned groups take the
+// next quadruple's first value instead of the previous one's last three) or,
+// with PART, the first n values with single stores.  nq: quadruples of the pool (slot 4 nq - 1 is the
 // reserved value and never written).
 template <int QT, int A, bool PART, typename OutT>
 __device__ __forceinline__ void group_emit(OutT *__restrict__ ob, const float2 (&y)[QT][2], float sc, uint32_t q0,
@@ -147,6 +148,24 @@ __device__ __forceinline__ void group_emit(OutT *__restrict__ ob, const float2 (
             if (pos + 3 < n) store1(rg, ob + pos + 3, v23.y);
             continue;
         }
+        const bool last = (j == QT - 1) && (q + 1u == nq);  // the quadruple holding the reserved slot
+        if (A == 3) {
+            // groups start one value into each quadruple: this quadruple's
+            // values 1..3 and the next one's value 0 -- one shuffle from the
+            // right neighbour (lane 0 lends its next j's value to lane 31)
+            // instead of three from the left
+            const float lend = (lane == 0 && j + 1 < QT) ? y[j + 1 < QT ? j + 1 : j][0].x * sc : v01.x;
+            const float nx = __shfl_sync(0xffffffffu, lend, (lane + 1u) & 31u);
+            if (j == 0 && lane == 0) store1(rg, ob + pos, v01.x);  // predecessor in another warp or before the block
+            if (!(l31 && j == QT - 1)) {
+                store4(rg, ob + pos + 1, v01.y, v23.x, v23.y, nx);
+            } else {  // the successor is in another warp, or slot pos + 3 is the reserved one
+                store1(rg, ob + pos + 1, v01.y);
+                store1(rg, ob + pos + 2, v23.x);
+                if (!last) store1(rg, ob + pos + 3, v23.y);
+            }
+            continue;
+        }
         float p1 = 0.f, p2 = 0.f, p3 = 0.f;
         if (A >= 1) p3 = __shfl_sync(0xffffffffu, l31 ? l3 : v23.y, src);
         if (A >= 2) p2 = __shfl_sync(0xffffffffu, l31 ? l2 : v23.x, src);
@@ -154,7 +173,6 @@ __device__ __forceinline__ void group_emit(OutT *__restrict__ ob, const float2 (
         l1 = v01.y;
         l2 = v23.x;
         l3 = v23.y;
-        const bool last = (j == QT - 1) && (q + 1u == nq);  // the quadruple holding the reserved slot
         if (A == 0) {
             if (!last) store4(rg, ob + pos, v01.x, v01.y, v23.x, v23.y);
             else {
