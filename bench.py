@@ -277,10 +277,11 @@ def other_workloads(wn, torch, dev, stream, flush, sm_mhz=None, headline_value=N
     wn.wn_set_cuda_stream(h1, stream)
     n1 = 1 << 24
     o1 = torch.empty(n1, dtype=torch.float32, device=dev)
-    shape1 = wn.wn_get_config(h1)  # the latency mode's default for one stream
+    shape1 = wn.wn_get_config_ex(h1)  # a lone stream's default: the chain mode
     wn.wn_generate_ex(o1, n1, h1, wn.WN_F32, stream)
     t1 = _timed(torch, stream, flush, lambda: wn.wn_generate_ex(o1, n1, h1, wn.WN_F32, stream), 5)
     res["single_stream"] = {"value": n1 / (t1 / 1e3), "unit": "variates/s", "ms_per_call": t1,
+                            "ns_per_block": t1 * 1e6 / math.ceil(n1 / 1023),
                             "config": "1 stream, pool N=1024, R=2, seed 1, 2^24 FP32 per call",
                             "shape": list(shape1)}
     wn.wn_destroy(h1)

@@ -299,6 +299,24 @@ wn_status wn_set_config(wn_stream *s, uint32_t quads_per_thread, uint32_t thread
  * does not start at window address 1024.
  */
 #define WN_CFG_GROUP 2u
+/*
+ * WN_CFG_CHAIN selects the chain-mode kernel, built for streams whose serial
+ * chain of blocks sets the time (Section 5.1: each block's pool is the
+ * previous block's output): threads / 32 compute warps run a stream's
+ * passes, each drawing its own permutations and signs one pass ahead, on two
+ * shared pool buffers (one barrier per pass); a further warp forms each
+ * block's scale (Section 5.5) from the block's sums of squares while the
+ * compute warps already run the next block, and a block's values are stored
+ * during the next block's first pass.  quads_per_thread is the quadruples
+ * per lane, with 128 * quads_per_thread * (threads / 32) = pool_N; compiled
+ * for (pool 1024: 2, 128 and 1, 256), (2048: 2, 256), (4096: 4, 256),
+ * (8192: 8, 256), (16384: 16, 256).  Launches of few streams of one
+ * pool size use it without being asked.  Values agree with the other kernels
+ * within the FP32 tolerance (sums of squares added in FP32, in another
+ * order); integer streams are identical.  WN_EINVAL for other shapes,
+ * variants, mixed pool sizes, or together with the other flags.
+ */
+#define WN_CFG_CHAIN 4u
 wn_status wn_set_config_ex(wn_stream *s, uint32_t quads_per_thread, uint32_t threads, uint32_t flags);
 
 /*
@@ -327,12 +345,11 @@ wn_status wn_autotune(wn_stream *s, uint64_t count, wn_dtype dtype, void *cuda_s
                       uint32_t *quads_per_thread, uint32_t *threads);
 
 /* wn_get_config -- the launch shape the next generate call will use (for a
- * handle of few streams, the latency mode's). */
+ * handle of few streams, the chain mode's or the latency mode's). */
 wn_status wn_get_config(const wn_stream *s, uint32_t *quads_per_thread, uint32_t *threads);
 
 /* wn_get_config_ex -- the same and its layout flags (WN_CFG_IN_PLACE,
- * WN_CFG_GROUP); any
- * output pointer may be NULL. */
+ * WN_CFG_GROUP, WN_CFG_CHAIN); any output pointer may be NULL. */
 wn_status wn_get_config_ex(const wn_stream *s, uint32_t *quads_per_thread, uint32_t *threads, uint32_t *flags);
 
 /* wn_num_streams -- number of streams in the handle (0 for NULL). */

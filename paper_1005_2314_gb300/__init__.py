@@ -25,7 +25,7 @@ __all__ = [
     "wn_create", "wn_create_streams", "wn_create_ex", "WN_CHI2", "WN_RESERVE", "WN_UPDATE", "wn_destroy", "wn_generate", "wn_generate_ex",
     "wn_generate_host",
     "wn_set_cuda_stream", "wn_set_config", "wn_get_config", "wn_set_config_ex", "wn_get_config_ex",
-    "WN_CFG_IN_PLACE", "WN_CFG_GROUP", "wn_autotune", "wn_gbm", "wn_generate_batch",
+    "WN_CFG_IN_PLACE", "WN_CFG_GROUP", "WN_CFG_CHAIN", "wn_autotune", "wn_gbm", "wn_generate_batch",
     "wn_autotune_batch", "wn_generate_batch_noalloc", "wn_get_batch_plan", "wn_set_batch_plan", "wn_num_streams", "wn_get_pool", "wn_get_state",
     "wn_rng_draws", "wn_debug_report", "wn_boxmuller", "wn_save", "wn_load", "wn_last_error", "library_path", "load",
 ]
@@ -33,6 +33,7 @@ __all__ = [
 WN_F32, WN_BF16, WN_F16 = 0, 1, 2
 WN_CFG_IN_PLACE = 1
 WN_CFG_GROUP = 2
+WN_CFG_CHAIN = 4
 WN_OK, WN_EINVAL, WN_ENOMEM, WN_ECUDA, WN_ETIMEOUT = 0, 1, 2, 3, 4
 _STATUS = {1: "WN_EINVAL", 2: "WN_ENOMEM", 3: "WN_ECUDA", 4: "WN_ETIMEOUT"}
 
@@ -264,7 +265,8 @@ def wn_get_config(h: Handle) -> tuple[int, int]:
 
 def wn_set_config_ex(h: Handle, quads_per_thread: int, threads: int, flags: int = 0) -> None:
     """wn_set_config with layout flags (WN_CFG_IN_PLACE: one pool buffer per CTA;
-    WN_CFG_GROUP: the group-mode kernel, threads / 32 warps per stream)."""
+    WN_CFG_GROUP: the group-mode kernel, threads / 32 warps per stream;
+    WN_CFG_CHAIN: the chain-mode kernel, threads / 32 compute warps per stream)."""
     _check(_L().wn_set_config_ex(h.ptr, quads_per_thread, threads, flags), "wn_set_config_ex")
 
 

@@ -16,6 +16,7 @@
 #include "wn_gen.cuh"
 #include "wn_group.cuh"
 #include "wn_emit.cuh"
+#include "wn_chain.cuh"
 #include "tune_cache.h"
 
 namespace wn {
@@ -218,7 +219,7 @@ bool cfg_ok(const LaunchCfg &c, uint32_t n_max)
 {
     bool compiled = false;
     for (const auto &k : wn::kShapes) compiled |= (k[0] == c.qt && k[1] == c.maxt && k[3] == c.ip);
-    return compiled && c.threads >= 32 && c.threads % 32 == 0 && c.threads + 32 <= (uint32_t)c.maxt &&
+    return compiled && c.grp == 0 && c.threads >= 32 && c.threads % 32 == 0 && c.threads + 32 <= (uint32_t)c.maxt &&
            (uint64_t)c.threads * c.qt >= n_max / 4;
 }
 
@@ -259,6 +260,44 @@ LaunchCfg group_cfg_of(uint32_t N, uint32_t G)
     LaunchCfg c{(int)(N / (128u * G)), (int)(32u * G), 32u * G, 1};
     c.grp = 1;
     return c;
+}
+
+// A compiled chain-mode shape (wn::kChainShapes) for pool N with G compute warps.
+bool chain_shape_ok(uint32_t N, uint32_t G)
+{
+    for (const auto &k : wn::kChainShapes)
+        if ((uint32_t)k[0] == N && (uint32_t)k[1] == G) return true;
+    return false;
+}
+
+// The chain-mode shape of pool N with G compute warps (plus the scale warp).
+LaunchCfg chain_cfg_of(uint32_t N, uint32_t G)
+{
+    LaunchCfg c{(int)(N / (128u * G)), (int)(32u * (G + 1)), 32u * G, 0};
+    c.grp = 2;
+    return c;
+}
+
+// Compute warps of the chain mode's default shape for pool N (false: none).
+bool chain_default(uint32_t N, uint32_t &G)
+{
+    switch (N) {
+    case 1024: G = 4; break;
+    case 2048:
+    case 4096:
+    case 8192:
+    case 16384: G = 8; break;
+    default: G = 0; return false;
+    }
+    return chain_shape_ok(N, G);
+}
+
+// The chain mode serves the plain method (any number of streams of one pool
+// size); its shared memory must fit one CTA.
+bool chain_fits(const wn_stream *s, uint32_t N, uint32_t G)
+{
+    return !s->var && chain_shape_ok(N, G) &&
+           wn::chain_smem_bytes(s->smem_base, N, G) <= (size_t)s->smem_optin;
 }
 
 // Pool sizes whose default launch is the group mode, with its warps per
@@ -335,6 +374,25 @@ bool latency_cfg_for(const wn_stream *s, LaunchCfg &out, uint32_t n_launch)
     return latency_default(s->n_max, out);
 }
 
+// The chain mode (wn_chain.cuh) for a generate launch of n_launch streams:
+// the handle's shape when it is a chain shape; with no shape set, the default
+// chain shape of the pool size for launches of few streams (each stream's
+// serial chain of blocks then sets the time).
+bool chain_cfg_for(const wn_stream *s, LaunchCfg &out, uint32_t n_launch)
+{
+    if (s->var || !s->uniform_N) return false;
+    if (s->has_cfg) {
+        if (s->cfg.grp != 2 || !chain_fits(s, s->n_max, s->cfg.threads / 32u)) return false;
+        out = s->cfg;
+        return true;
+    }
+    uint32_t G = 0;
+    if (n_launch > (uint32_t)std::max(1, s->sms / 2) || !chain_default(s->n_max, G) || !chain_fits(s, s->n_max, G))
+        return false;
+    out = chain_cfg_of(s->n_max, G);
+    return true;
+}
+
 // --- the autotuners' choices across processes (tune_cache.cu) -------------
 // The device's name and SM count, the first part of every key.
 std::string device_tag(const wn_stream *s)
@@ -372,7 +430,9 @@ bool cfg_from_text(const char *t, LaunchCfg &c)
 // A shape read from the file is used only if this library compiled it.
 bool cached_cfg_ok(const LaunchCfg &c, uint32_t N)
 {
-    if (c.grp) return c.threads % 32 == 0 && group_shape_ok(N, c.threads / 32u) && c.ip == 1 &&
+    if (c.grp == 2) return c.threads % 32 == 0 && chain_shape_ok(N, c.threads / 32u) && c.ip == 0 &&
+                           (uint64_t)128u * c.qt * (c.threads / 32u) == N;
+    if (c.grp) return c.grp == 1 && c.threads % 32 == 0 && group_shape_ok(N, c.threads / 32u) && c.ip == 1 &&
                       (uint64_t)128u * c.qt * (c.threads / 32u) == N;
     return cfg_ok(c, N);
 }
@@ -391,6 +451,7 @@ bool cached_gen_cfg(const wn_stream *s, wn_dtype dt, LaunchCfg &c)
     std::string v;
     if (!wn::tune_cache_get(gen_key(s, dt), v) || !cfg_from_text(v.c_str(), c) || !cached_cfg_ok(c, s->n_max))
         return false;
+    if (c.grp == 2) return s->uniform_N && chain_fits(s, s->n_max, c.threads / 32u);
     return !c.grp || group_eligible(s);
 }
 
@@ -411,6 +472,18 @@ wn_status launch_generate(wn_stream *s, void *out, uint64_t count, uint32_t warm
     a.warmup_blocks = warmup;
     cudaError_t e;
     LaunchCfg lc;
+    if (warmup == 0 && count > 0 && chain_cfg_for(s, lc, a.n_streams)) {
+        const uint32_t G = lc.threads / 32u;
+        const size_t smem = wn::chain_smem_bytes(s->smem_base, s->n_max, G);
+        switch (dt) {
+        case WN_F32: e = wn::launch_chain_f32(a, s->n_max, G, smem, cs); break;
+        case WN_BF16: e = wn::launch_chain_bf16(a, s->n_max, G, smem, cs); break;
+        case WN_F16: e = wn::launch_chain_f16(a, s->n_max, G, smem, cs); break;
+        default: return fail(WN_EINVAL, "unknown dtype");
+        }
+        if (e != cudaSuccess) return cuda_fail("generate launch (chain mode)", e);
+        return WN_OK;
+    }
     if (warmup == 0 && count > 0 && latency_cfg_for(s, lc, a.n_streams)) {
         // the two-control-warp kernel up to two passes per block, the emitter
         // kernel (wn_emit.cuh) above (see launch_persist_latency)
@@ -429,8 +502,8 @@ wn_status launch_generate(wn_stream *s, void *out, uint64_t count, uint32_t warm
         if (e != cudaSuccess) return cuda_fail("generate launch (latency mode)", e);
         return WN_OK;
     }
-    LaunchCfg c = s->has_cfg ? s->cfg : default_cfg(s);
-    if (c.grp && warmup == 0 && group_eligible(s)) {
+    LaunchCfg c = s->has_cfg && s->cfg.grp != 2 ? s->cfg : default_cfg(s);
+    if (c.grp == 1 && warmup == 0 && group_eligible(s)) {
         const uint32_t G = c.threads / 32u;
         switch (dt) {
         case WN_F32: e = wn::launch_group_f32(a, s->n_max, G, s->sms, cs, &s->group_ctas); break;
@@ -728,6 +801,20 @@ wn_status enqueue_batch(wn_stream *s, const std::vector<Group> &groups, void *ou
         const bool want_lat = g.exclusive ? s->batch_lat >= 1
                                           : (tuned != s->group_lat.end() ? tuned->second
                                                                          : s->batch_lat >= 2 && !batch_cfg(s, g.N).grp);
+        uint32_t cg = 0;
+        if (g.exclusive && chain_default(g.N, cg) && chain_fits(s, g.N, cg)) {
+            // the longest chains: the chain mode, at most batch_density CTAs per SM
+            const size_t csm = chain_smem(s, wn::chain_smem_bytes(s->smem_base, g.N, cg));
+            switch (dt) {
+            case WN_F32: e = wn::launch_persist_chain_f32(a, bq, g.N, cg, csm, s->sms, b); break;
+            case WN_BF16: e = wn::launch_persist_chain_bf16(a, bq, g.N, cg, csm, s->sms, b); break;
+            default: e = wn::launch_persist_chain_f16(a, bq, g.N, cg, csm, s->sms, b); break;
+            }
+            if (e != cudaSuccess) return cuda_fail("wn_generate_batch: launch (chain mode)", e);
+            WN_CU(cudaEventRecord(s->join[gi], b));
+            WN_CU(cudaStreamWaitEvent(cs, s->join[gi], 0));
+            continue;
+        }
         if (!s->var && want_lat && latency_default(g.N, lc)) {
             e = launch_persist_latency(s, a, bq, lc, g.N, g.r_max, g.exclusive, dt, b);
             if (e != cudaSuccess) return cuda_fail("wn_generate_batch: launch", e);
@@ -1098,9 +1185,25 @@ void wn_destroy(wn_stream *s)
 wn_status wn_set_config_ex(wn_stream *s, uint32_t quads_per_thread, uint32_t threads, uint32_t flags)
 {
     if (!s) return fail(WN_EINVAL, "wn_set_config: NULL handle");
-    if (flags & ~(uint32_t)(WN_CFG_IN_PLACE | WN_CFG_GROUP)) return fail(WN_EINVAL, "wn_set_config_ex: unknown flags");
+    if (flags & ~(uint32_t)(WN_CFG_IN_PLACE | WN_CFG_GROUP | WN_CFG_CHAIN))
+        return fail(WN_EINVAL, "wn_set_config_ex: unknown flags");
     if (quads_per_thread == 0 && threads == 0) {
         s->has_cfg = false;
+        return WN_OK;
+    }
+    if (flags & WN_CFG_CHAIN) {
+        const uint32_t G = threads / 32u;
+        if ((flags & (WN_CFG_GROUP | WN_CFG_IN_PLACE)) || threads % 32u != 0 || G == 0 ||
+            !chain_shape_ok(s->n_max, G) || (uint64_t)128u * quads_per_thread * G != s->n_max)
+            return fail(WN_EINVAL, "wn_set_config_ex: no compiled chain-mode shape with " +
+                                       std::to_string(quads_per_thread) + " quadruples per lane and " +
+                                       std::to_string(threads) + " compute threads covers pool " +
+                                       std::to_string(s->n_max));
+        if (s->var || !s->uniform_N || !chain_fits(s, s->n_max, G))
+            return fail(WN_EINVAL, "wn_set_config_ex: the chain mode needs one pool size, the plain method and "
+                                   "room for two pool buffers in one CTA's shared memory");
+        s->cfg = chain_cfg_of(s->n_max, G);
+        s->has_cfg = true;
         return WN_OK;
     }
     if (flags & WN_CFG_GROUP) {
@@ -1189,6 +1292,10 @@ wn_status wn_autotune(wn_stream *s, uint64_t count, wn_dtype dtype, void *cuda_s
     if (group_eligible(s))  // the compiled group-mode shapes of this pool size
         for (const auto &k : wn::kGroupShapes)
             if ((uint32_t)k[0] == s->n_max) cand.push_back(group_cfg_of(s->n_max, (uint32_t)k[1]));
+    if (s->uniform_N)  // and the chain-mode ones
+        for (const auto &k : wn::kChainShapes)
+            if ((uint32_t)k[0] == s->n_max && chain_fits(s, s->n_max, (uint32_t)k[1]))
+                cand.push_back(chain_cfg_of(s->n_max, (uint32_t)k[1]));
     if (cand.empty()) return fail(WN_EINVAL, "wn_autotune: no compiled shape fits");
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(cuda_stream);
     const size_t esize = dtype == WN_F32 ? 4 : 2;
@@ -1270,10 +1377,13 @@ wn_status wn_get_config_ex(const wn_stream *s, uint32_t *quads_per_thread, uint3
 {
     if (!s) return fail(WN_EINVAL, "wn_get_config: NULL handle");
     LaunchCfg c = s->has_cfg ? s->cfg : default_cfg(s), lc;
-    if (latency_cfg_for(s, lc, s->n)) c = lc;  // few streams: the latency mode's shape
+    if (chain_cfg_for(s, lc, s->n)) c = lc;           // few streams of one pool size: the chain mode
+    else if (latency_cfg_for(s, lc, s->n)) c = lc;  // few streams: the latency mode's shape
     if (quads_per_thread) *quads_per_thread = (uint32_t)c.qt;
     if (threads) *threads = c.threads;
-    if (flags) *flags = (c.ip ? (uint32_t)WN_CFG_IN_PLACE : 0u) | (c.grp ? (uint32_t)WN_CFG_GROUP : 0u);
+    if (flags)
+        *flags = (c.ip ? (uint32_t)WN_CFG_IN_PLACE : 0u) | (c.grp == 1 ? (uint32_t)WN_CFG_GROUP : 0u) |
+                 (c.grp == 2 ? (uint32_t)WN_CFG_CHAIN : 0u);
     return WN_OK;
 }
 

@@ -125,7 +125,7 @@ def test_in_place_rejected_where_not_compiled(wn):
     with pytest.raises(wn.WnError):
         wn.wn_set_config_ex(h, 8, 128, wn.WN_CFG_IN_PLACE)  # no in-place kernel with 8 quadruples per thread
     with pytest.raises(wn.WnError):
-        wn.wn_set_config_ex(h, 16, 64, 4)  # unknown flag
+        wn.wn_set_config_ex(h, 16, 64, 8)  # unknown flag
 
 
 def test_default_shapes(wn):

@@ -280,7 +280,7 @@ def test_rejects_uncompiled_shape(wn):
     with pytest.raises(wn.WnError):
         wn.wn_set_config(h, 3, 512)
     wn.wn_set_config(h, 0, 0)
-    assert wn.wn_get_config(h) == (8, 128)
+    assert wn.wn_get_config(h) == (4, 256)  # a lone stream's default: the chain mode, 8 compute warps
 
 
 def test_autotune_keeps_sequence_and_matches_oracle(wn, torch):
