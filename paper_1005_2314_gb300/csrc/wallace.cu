@@ -297,7 +297,7 @@ bool chain_default(uint32_t N, uint32_t &G)
 bool chain_fits(const wn_stream *s, uint32_t N, uint32_t G)
 {
     return !s->var && chain_shape_ok(N, G) &&
-           wn::chain_smem_bytes(s->smem_base, N, G) <= (size_t)s->smem_optin;
+           wn::chain_smem_bytes(s->smem_base, N, G, s->r_max) <= (size_t)s->smem_optin;
 }
 
 // Pool sizes whose default launch is the group mode, with its warps per
@@ -474,7 +474,7 @@ wn_status launch_generate(wn_stream *s, void *out, uint64_t count, uint32_t warm
     LaunchCfg lc;
     if (warmup == 0 && count > 0 && chain_cfg_for(s, lc, a.n_streams)) {
         const uint32_t G = lc.threads / 32u;
-        const size_t smem = wn::chain_smem_bytes(s->smem_base, s->n_max, G);
+        const size_t smem = wn::chain_smem_bytes(s->smem_base, s->n_max, G, s->r_max);
         switch (dt) {
         case WN_F32: e = wn::launch_chain_f32(a, s->n_max, G, smem, cs); break;
         case WN_BF16: e = wn::launch_chain_bf16(a, s->n_max, G, smem, cs); break;
@@ -804,7 +804,7 @@ wn_status enqueue_batch(wn_stream *s, const std::vector<Group> &groups, void *ou
         uint32_t cg = 0;
         if (g.exclusive && chain_default(g.N, cg) && chain_fits(s, g.N, cg)) {
             // the longest chains: the chain mode, at most batch_density CTAs per SM
-            const size_t csm = chain_smem(s, wn::chain_smem_bytes(s->smem_base, g.N, cg));
+            const size_t csm = chain_smem(s, wn::chain_smem_bytes(s->smem_base, g.N, cg, g.r_max));
             switch (dt) {
             case WN_F32: e = wn::launch_persist_chain_f32(a, bq, g.N, cg, csm, s->sms, b); break;
             case WN_BF16: e = wn::launch_persist_chain_bf16(a, bq, g.N, cg, csm, s->sms, b); break;

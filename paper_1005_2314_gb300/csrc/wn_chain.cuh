@@ -6,42 +6,45 @@
 // A stream's blocks form one dependency chain through its pool (Section 5.1),
 // but the chain itself is only the passes: a block's scale comes from the
 // block before it (Section 5.5), and its values leave the pool untouched.  So
-// a CTA runs the passes on G compute warps, and two more warps do the rest
-// while the compute warps run the next block:
-//  * every compute warp draws each pass's permutation and signs itself
-//    (Sections 5.2, 5.4, 5.8), one pass ahead, from its own copy of the
-//    stream's generator -- no pass tables, no table hand-over;
+// a CTA runs the passes on G compute warps, and helper warps do the rest
+// beside them:
+//  * the draw warp draws each pass's permutation and signs (Sections 5.2,
+//    5.4, 5.8) from the stream's generator into a ring of pass words, blocks
+//    ahead; a compute warp loads the next pass's words during the pass;
 //  * a pass reads one shared pool buffer and writes another, so one barrier
 //    among the compute warps ends it: the passes of a block alternate
-//    between two work buffers, and the final pass writes one of two emission
-//    buffers (by the block's parity), which the next block's first pass
-//    reads;
+//    between two work buffers, and the final pass writes emission buffer
+//    b mod KS (KS = 4, or 2 for pools of 8192), which the next block's first
+//    pass reads;
 //  * the scale warp (warp G) adds the block's per-lane sums of squares and
 //    forms the next block's scale;
 //  * NS store warps (warps G+1 .. G+NS, store warp s taking the blocks
-//    b = s mod NS) read a block's values from its emission buffer, scale them into a
-//    staging buffer laid out like the output (16-byte chunks of the output at
-//    16-byte boundaries), and write the whole chunks with one bulk copy of
-//    the tensor-memory-access unit (cp.async.bulk), the partial chunk at each
-//    end (shared with the neighbouring block) with plain stores.  Bulk copies
-//    belong to the asynchronous proxy, which no barrier waits on.
+//    b = s mod NS) read a block's values from its emission buffer, scale
+//    them into a staging buffer laid out like the output (16-byte chunks of
+//    the output at 16-byte boundaries), and write the whole chunks with one
+//    bulk copy of the tensor-memory-access unit (cp.async.bulk), the partial
+//    chunk at each end (shared with the neighbouring block) with plain
+//    stores.  Bulk copies belong to the asynchronous proxy, which no barrier
+//    waits on.
 // Hand-overs: at PART(b) the compute warps arrive with block b's sums of
-// squares and reserved value (its emission buffer written), the scale warp
-// and block b's store warp wait; at SCALE(b) those two arrive (block b's sums
-// read; its emission buffer read), the compute warps wait at the end of block
-// b+1, before their next write to those buffers -- so a store warp, whose
-// staging must end by then, has NS blocks for all of its work; at SC(b) the
+// squares and reserved value (its emission buffer written), the scale warp,
+// block b's store warp and the draw warp wait; at SCALE(b) those three arrive
+// (block b's sums read; its emission buffer read; block b + KS + 1's pass
+// words written), and the compute warps wait at the end of block b + KS - 1,
+// before they next overwrite those buffers -- so a store warp has KS - 1
+// blocks for its staging and NS blocks for all of its work; at SC(b) the
 // scale warp hands block b+1's scale to block b+1's store warp.  Only the
 // store warps wait for a scale.
-// Pools above 8192 values leave no room for four pool buffers and the staging
-// buffers; there the passes alternate between two buffers and the compute
-// warps store each block's values themselves early in the next block's
-// first pass (realigned by warp shuffles), and the store warps only keep the
+// Pools above 8192 values leave no room for the emission and staging
+// buffers; there the passes alternate between two buffers, the compute warps
+// store each block's values themselves early in the next block's first pass
+// (realigned by warp shuffles), KS = 2, and the store warps only keep the
 // barrier counts.
-// Barrier identifiers cycle with the block index (PART, SCALE: b mod NS; SC:
-// b mod 14 - 2 NS), so that no barrier ever has two phases open; the scales
-// are kept in 2 NS slots (b mod 2 NS) for the same reason.  No wait spins: every barrier is a hardware named
-// barrier whose arrivals are fixed by the block count all warps share.
+// Barrier identifiers cycle with the block index (PART, SCALE: b mod
+// max(NS, KS); SC: the rest of the 16), so that no barrier ever has two
+// phases open; the scales are kept in 2 NS slots (b mod 2 NS) for the same
+// reason.  No wait spins: every barrier is a hardware named barrier whose
+// arrivals are fixed by the block count all warps share.
 #pragma once
 
 #include "wn_group.cuh"
@@ -49,14 +52,15 @@
 namespace wn {
 
 // Named barriers of the chain mode (0 is __syncthreads): the pass barrier
-// among the compute warps, then PART, SCALE and SC.
-// With NS store warps: PART(b) has identifier 2 + b mod NS, SCALE(b)
-// 2 + NS + b mod NS, SC(b) 2 + 2 NS + b mod (14 - 2 NS) -- every one of the 16.
+// among the compute warps, then PART, SCALE and SC (with MP = max(NS, KS):
+// PART(b) has identifier 2 + b mod MP, SCALE(b) 2 + MP + b mod MP, SC(b)
+// 2 + 2 MP + b mod (14 - 2 MP) -- every one of the 16).
 constexpr uint32_t kChPass = 1;
 // Store warps: four beside four compute warps (pools of 1024, whose blocks are
 // short), two beside eight (the registers allow no more warps).
 __host__ __device__ constexpr uint32_t chain_store_warps(uint32_t G) { return G <= 4u ? 4u : 2u; }
-__host__ __device__ constexpr uint32_t chain_threads(uint32_t G) { return 32u * (G + 1u + chain_store_warps(G)); }
+// Threads: the compute warps, the scale warp, the store warps, the draw warp.
+__host__ __device__ constexpr uint32_t chain_threads(uint32_t G) { return 32u * (G + 2u + chain_store_warps(G)); }
 
 // Small area at the window base: per-lane sums of squares [4][32 G] (by the
 // block's index modulo the emission buffers), then the reserved values [4],
@@ -79,13 +83,54 @@ __host__ __device__ constexpr uint32_t chain_stage_bytes(uint32_t N) { return ((
 // reading a block's values while the compute warps run the next three), two
 // for 8192 (shared memory).
 __host__ __device__ constexpr uint32_t chain_emit_bufs(uint32_t N) { return N <= 4096u ? 4u : 2u; }
-__host__ __device__ inline size_t chain_smem_bytes(uint32_t base, uint32_t N, uint32_t G)
+// Blocks from PART(b) to the compute warps' wait at SCALE(b): the emission
+// buffers with staging, else 2.  The draw warp keeps this many blocks' pass
+// words plus two in its ring.
+__host__ __device__ constexpr uint32_t chain_lag(uint32_t N) { return chain_stages(N) ? chain_emit_bufs(N) : 2u; }
+__host__ __device__ constexpr uint32_t chain_ring(uint32_t N) { return chain_lag(N) + 2u; }
+// Shared memory of a chain-mode CTA for pool N, G compute warps and up to
+// r_max passes per block: the pool, emission and staging buffers, then the
+// ring of pass words (16 bytes per pass).
+__host__ __device__ inline size_t chain_smem_bytes(uint32_t base, uint32_t N, uint32_t G, uint32_t r_max)
 {
     return (size_t)chain_window(base, N, G) +
            (chain_stages(N) ? 4u * (size_t)N * (2u + chain_emit_bufs(N)) +
                                   chain_store_warps(G) * (size_t)chain_stage_bytes(N)
-                            : 8u * (size_t)N) -
-           base;
+                            : 8u * (size_t)N) +
+           16u * (size_t)chain_ring(N) * r_max - base;
+}
+
+__device__ __forceinline__ void sts4u(uint32_t a, uint4 v)
+{
+    if (!dbg_shared_ok(a, 16)) return;
+    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w));
+}
+
+// One pass's words: alpha, gamma and the sign word (low, high) from the
+// pass's two draws (Sections 5.2, 5.4, 5.8).
+__device__ __forceinline__ uint4 pass_words(uint64_t &gx, uint64_t &gw, uint32_t N)
+{
+    const uint64_t wa = draw(gx, gw);
+    const uint64_t ws = draw(gx, gw);
+    return make_uint4(((uint32_t)(wa >> 32) & (N - 1)) | 1u, (uint32_t)wa & (N - 1), (uint32_t)ws,
+                      (uint32_t)(ws >> 32));
+}
+
+// A thread's pass quantities from the pass words (as group_pass derives them
+// from the draws).
+__device__ __forceinline__ GroupPass pass_from_words(uint4 t, uint32_t N, uint32_t q0, uint32_t lane)
+{
+    GroupPass p;
+    p.B0 = 4u * (t.x * q0 + t.y);
+    p.d1 = (t.x & 3u) * N;
+    p.dq = 128u * t.x;
+    const uint32_t word = (lane & 8u) ? t.w : t.z;
+    const uint32_t nib = (word >> (4u * (lane & 7u))) & 15u;
+    p.m01 = make_float2(neg_sign_one(nib & 1u), neg_sign_one((nib >> 1) & 1u));
+    p.m23 = make_float2(neg_sign_one((nib >> 2) & 1u), neg_sign_one(nib >> 3));
+    p.h01 = fmul2(p.m01, make_float2(-0.5f, -0.5f));
+    p.h23 = fmul2(p.m23, make_float2(-0.5f, -0.5f));
+    return p;
 }
 
 __device__ __forceinline__ void bar_arrive_n(uint32_t id, uint32_t n)
@@ -286,26 +331,29 @@ __device__ __forceinline__ void chain_stage_block(uint32_t st, uint32_t eb, uint
 // output, out_off elements past a 16-byte boundary.
 template <int G, int QT, typename OutT>
 __device__ __forceinline__ void run_stream_chain(StreamHdr *__restrict__ h, float *__restrict__ pool_g,
-                                                 OutT *__restrict__ out, uint64_t out_off, uint64_t count)
+                                                 OutT *__restrict__ out, uint64_t out_off, uint64_t count,
+                                                 uint32_t r_max)
 {
     constexpr uint32_t N = 128u * QT * G, nq = N / 4, NS = chain_store_warps(G), NT = chain_threads(G);
     constexpr bool STAGE = chain_stages(N);
     // KS: blocks from PART(b) to the compute warps' wait at SCALE(b) (the
     // emission buffers with staging, else 2); MP: identifiers of PART and of
     // SCALE; MSC: of SC
-    constexpr uint32_t KS = STAGE ? chain_emit_bufs(N) : 2u, MP = NS > KS ? NS : KS, MSC = 14u - 2u * MP;
+    constexpr uint32_t KS = chain_lag(N), MP = NS > KS ? NS : KS, MSC = 14u - 2u * MP, RK = chain_ring(N);
     constexpr uint32_t kPart = 2u, kScale = 2u + MP, kSc = 2u + 2u * MP;
-    constexpr uint32_t NH = 32u * (G + 2), ES = sizeof(OutT);  // NH: PART and SCALE
+    constexpr uint32_t NH = 32u * (G + 3), ES = sizeof(OutT);  // NH: PART and SCALE (all but NS - 1 store warps)
     static_assert(MSC >= NS + 1u, "SC needs NS + 1 identifiers");
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t base = smem_base();
     uint32_t dyn;
     asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
     // pool buffers: work W[0], W[1], then (with STAGE) emission E[0 .. KS-1],
-    // then the staging buffers T[0 .. NS-1]
+    // the staging buffers T[0 .. NS-1]; then the ring of pass words,
+    // [RK][r_max] (block b's in slot b mod RK)
     const uint32_t W = chain_window(base, N, G), SB = chain_stage_bytes(N);
-    const uint32_t E0 = W + 8u * N, T0 = E0 + 4u * N * KS;
-    if (dyn < chain_smem_bytes(base, N, G) || h->N != N) {  // not this kernel's layout
+    const uint32_t E0 = W + 8u * N, T0 = E0 + 4u * N * KS, TB = STAGE ? T0 + NS * SB : W + 8u * N;
+    const uint32_t R = h->R;
+    if (dyn < chain_smem_bytes(base, N, G, r_max) || h->N != N || R > r_max) {  // not this kernel's layout
         if (tid == 0) h->flags |= 1u;
         return;
     }
@@ -329,26 +377,32 @@ __device__ __forceinline__ void run_stream_chain(StreamHdr *__restrict__ h, floa
     const uint64_t nb = (count - n0 + (N - 2)) / (N - 1);
     const uint64_t tail = (count - n0) % (N - 1);  // values of a partial last block (0: whole)
     const uint64_t g0 = out_off + n0;              // output position of block 0's first value
-    const uint32_t R = h->R;
     // block 0's scale: the stored sum of squares and reserved value
     if (tid == 0) scs[0] = nb > 0 ? group_scale(h->sumsq, (float)h->r, (float)h->A, (float)h->B, N) : sc_prev;
+    const uint32_t dw = G + 1u + NS;  // the draw warp
+    uint64_t gx = h->x, gw = h->w;    // its generator
+    if (warp == dw)                   // the first blocks' pass words
+        for (uint64_t b = 0; b < nb && b <= KS; ++b)
+            for (uint32_t p = 0; p < R; ++p) {
+                const uint4 t = pass_words(gx, gw, N);
+                if (lane == (p & 31u)) sts4u(TB + 16u * ((uint32_t)b * r_max + p), t);
+            }
     __syncthreads();
     for (uint64_t i = tid; i < n0; i += NT) store1(rg, out + i, sc_prev * lds(P0 + 4u * (uint32_t)(k0 + i)));
     __syncthreads();  // the stored pool is read: it may be overwritten
 
-    uint64_t sx = h->x, sw = h->w;  // the generator after the last pass used
     if (warp < G) {
         const uint32_t q0 = warp * 32u * QT + lane;
         const uint32_t m4 = 4u * N - 1u, half = 2u * N;
-        uint64_t gx = sx, gw = sw;
         uint64_t e = g0;  // without STAGE: output position of the block whose values y hold
         float2 y[QT][2];
 #pragma unroll
         for (int j = 0; j < QT; ++j) y[j][0] = y[j][1] = make_float2(0.f, 0.f);
         uint32_t cur = P0;            // the buffer holding the pool
-        uint32_t kb = 0, kp = 0;      // b mod KS, b mod MP
-        GroupPass gp = group_pass(gx, gw, N, q0, lane);
+        uint32_t kb = 0, kp = 0, kt = 0;  // b mod KS, b mod MP, b mod RK
+        GroupPass gp = pass_from_words(lds4u(TB), N, q0, lane);
         for (uint64_t b = 0; b < nb; ++b) {
+            const uint32_t kt1 = kt + 1u == RK ? 0u : kt + 1u;
             for (uint32_t p = 0; p < R; ++p) {
                 uint32_t wr;
                 if (STAGE) wr = p + 1 == R ? E0 + 4u * N * kb : W + 4u * N * (p & 1u);
@@ -368,9 +422,9 @@ __device__ __forceinline__ void run_stream_chain(StreamHdr *__restrict__ h, floa
                                          (uint32_t)(e & 3u), 0, rg);
                     e += N - 1;
                 }
-                sx = gx;
-                sw = gw;
-                const GroupPass gn = group_pass(gx, gw, N, q0, lane);  // the next pass's, one ahead
+                // the next pass's words: of pass p+1, or of the next block's first
+                const uint32_t tn = p + 1 < R ? TB + 16u * (kt * r_max + p + 1u) : TB + 16u * kt1 * r_max;
+                const GroupPass gn = pass_from_words(lds4u(tn), N, q0, lane);
 #pragma unroll
                 for (int j = 0; j < QT; ++j) {
                     const float2 a01 = make_float2(av[j][0], av[j][1]), a23 = make_float2(av[j][2], av[j][3]);
@@ -396,6 +450,7 @@ __device__ __forceinline__ void run_stream_chain(StreamHdr *__restrict__ h, floa
                     else bar_wait(kChPass, 32u * G);
                     kb = kb + 1 == KS ? 0u : kb + 1;
                     kp = kp + 1 == MP ? 0u : kp + 1;
+                    kt = kt1;
                 } else {
                     bar_wait(kChPass, 32u * G);  // the pass's stores precede the next pass's gathers
                 }
@@ -444,6 +499,24 @@ __device__ __forceinline__ void run_stream_chain(StreamHdr *__restrict__ h, floa
                 fin[1] = r;
             }
         }
+    } else if (warp == dw) {
+        // the draw warp: once block b is done, block b + KS + 1's pass words
+        // (the compute warps read them after SCALE(b))
+        for (uint64_t b = 0; b < nb; ++b) {
+            bar_wait(kPart + (uint32_t)(b % MP), NH);
+            if (b + KS + 1 < nb) {
+                const uint32_t slot = (uint32_t)((b + KS + 1) % RK);
+                for (uint32_t p = 0; p < R; ++p) {
+                    const uint4 t = pass_words(gx, gw, N);
+                    if (lane == (p & 31u)) sts4u(TB + 16u * (slot * r_max + p), t);
+                }
+            }
+            if (b + KS <= nb) bar_arrive_n(kScale + (uint32_t)(b % MP), NH);
+        }
+        if (nb > 0 && lane == 0) {  // the generator after the call's last pass
+            h->x = gx;
+            h->w = gw;
+        }
     } else {
         // store warp s (warp G+1+s): the blocks b = s mod NS -- block b's
         // values from its emission buffer, scaled (block b's scale: from the
@@ -482,8 +555,6 @@ __device__ __forceinline__ void run_stream_chain(StreamHdr *__restrict__ h, floa
     }
     if (tid == 0) {
         if (nb > 0) {
-            h->x = sx;
-            h->w = sw;
             h->sumsq = (double)fin[0];
             h->r = (double)fin[1];
             h->scale = scs[(uint32_t)((nb - 1) % (2u * NS))];
@@ -503,7 +574,8 @@ __global__ void __launch_bounds__(chain_threads(G), 1) chain_kernel(GenArgs a)
 {
     StreamHdr *h = a.hdr + blockIdx.x;
     const uint64_t off = (uint64_t)blockIdx.x * a.out_stride;
-    run_stream_chain<G, QT, OutT>(h, a.pools + h->pool_off, reinterpret_cast<OutT *>(a.out) + off, off, a.count);
+    run_stream_chain<G, QT, OutT>(h, a.pools + h->pool_off, reinterpret_cast<OutT *>(a.out) + off, off, a.count,
+                                  a.r_max);
 }
 
 // Persistent chain-mode kernel (a batch's longest requests): each CTA claims
@@ -524,7 +596,7 @@ __global__ void __launch_bounds__(chain_threads(G), 1) persist_chain_kernel(GenA
         StreamHdr *h = a.hdr + si;
         const uint64_t off = bq.offsets[si];
         run_stream_chain<G, QT, OutT>(h, a.pools + h->pool_off, reinterpret_cast<OutT *>(a.out) + off, off,
-                                      bq.counts[si]);
+                                      bq.counts[si], a.r_max);
     }
 }
 

@@ -62,8 +62,9 @@ class Buffer:
 
 
 def simulate(G, R, nb, stage, rng, NS=2, KE=2):
-    H = G + 2  # one hand-over: the compute warps, the scale warp, one store warp
+    H = G + 3  # PART, SCALE: the compute warps, the scale warp, one store warp, the draw warp
     KS = KE if stage else 2  # blocks from PART(b) to the compute warps' wait at SCALE(b)
+    RK = KS + 2  # slots of the ring of pass words
     MP = max(NS, KS)  # PART and SCALE identifiers
     MSC = 14 - 2 * MP  # SC identifiers
     bars = {"pass": Barrier(G)}
@@ -83,6 +84,27 @@ def simulate(G, R, nb, stage, rng, NS=2, KE=2):
     scs[0] = ("sc", 0)
     scs_pending = {("sc", 0): {"s0"} if stage else set(comp)}
     bulks = {k: [] for k in range(NS)}  # per store warp: [block, read_done]
+    # the ring of pass words: slot -> (block, compute warps yet to read it)
+    ring = {}
+
+    def write_words(blk):
+        slot = blk % RK
+        if slot in ring:
+            old, pending = ring[slot]
+            assert not pending, f"pass words of block {old} overwritten before {pending} read them"
+        ring[slot] = (blk, set(comp))
+
+    def read_words(me, blk):
+        got, _ = ring.get(blk % RK, (None, set()))
+        assert got == blk, f"{me} expected the pass words of block {blk}, found block {got}"
+
+    def done_words(me, blk):  # the warp's last read of block blk's words is behind it
+        got, pending = ring[blk % RK]
+        assert got == blk
+        pending.discard(me)
+
+    for blk in range(min(nb, KS + 1)):  # before the CTA's first barrier
+        write_words(blk)
 
     def sync(name, label):
         g = bars[name].arrive(label)
@@ -92,6 +114,8 @@ def simulate(G, R, nb, stage, rng, NS=2, KE=2):
     def compute(w):
         me = comp[w]
         cur = pool_buf
+        if nb > 0:
+            read_words(me, 0)
         for b in range(nb):
             for p in range(R):
                 rd = cur
@@ -101,6 +125,11 @@ def simulate(G, R, nb, stage, rng, NS=2, KE=2):
                     wr = "W1" if cur == "W0" else "W0"
                 prev = ("pool",) if (b == 0 and p == 0) else ((b - 1, R - 1) if p == 0 else (b, p - 1))
                 bufs[rd].read(me, prev)
+                yield
+                if p + 1 < R:  # the next pass's words, loaded during this pass
+                    read_words(me, b)
+                elif b + 1 < nb:
+                    read_words(me, b + 1)
                 yield
                 if not stage and p == 0 and b > 0:  # the previous block's values, scaled
                     assert scs[(b - 1) % K] == ("sc", b - 1), f"{me} emits block {b - 1} with {scs[(b - 1) % K]}"
@@ -112,6 +141,7 @@ def simulate(G, R, nb, stage, rng, NS=2, KE=2):
                 bufs[wr].write(w, (b, p), readers)
                 yield
                 if last_pass:
+                    done_words(me, b)
                     parts[b % KS].write(w, ("parts", b), ["scale"])
                     bars[f"P{b % MP}"].arrive(("P", b))
                     yield
@@ -170,7 +200,17 @@ def simulate(G, R, nb, stage, rng, NS=2, KE=2):
         while not all(done for _, done in bulks[sp]):  # wait_group 0
             yield
 
-    actors = [compute(w) for w in range(G)] + [scale()] + [store(k) for k in range(NS)]
+    def drawer():
+        for b in range(nb):
+            yield from sync(f"P{b % MP}", ("P", b))
+            if b + KS + 1 < nb:
+                write_words(b + KS + 1)
+                yield
+            if b + KS <= nb:
+                bars[f"S{b % MP}"].arrive(("S", b))
+                yield
+
+    actors = [compute(w) for w in range(G)] + [scale()] + [store(k) for k in range(NS)] + [drawer()]
     steps = 0
     while actors:
         # the bulk copies' reads complete at random times
