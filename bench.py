@@ -515,6 +515,7 @@ def run_ours(args, rank, world, local_rank):
         bout = torch.empty(btotal, dtype=torch.float32, device=dev)
         hb = wn.wn_create_streams(bN, bR, [rank * 10000 + i + 1 for i in range(10000)], WARMUP_BLOCKS, stream)
         wn.wn_autotune_batch(bout, bc, boff, hb, wn.WN_F32, stream)
+        plan = wn.wn_get_batch_plan(hb)
         wn.wn_generate_batch(bout, bc, boff, hb, wn.WN_F32, True, stream)  # captures the graph
         torch.cuda.synchronize()
         bms = []
@@ -533,6 +534,7 @@ def run_ours(args, rank, world, local_rank):
                    "replays": len(bts), "variates_per_replay": btotal, "streams": 10000,
                    "achieved_gbs": round(btotal * 4 / (bt / 1e3) / 1e9, 1),
                    "longest_request": int(bc.max()),
+                   "plan": {"chains": int(plan[0]), "chains_per_sm": int(plan[1])},
                    "how": "wn_generate_batch with use_graph: per pool size one persistent kernel (atomic claim, "
                           "longest request first), groups forked on branch streams, captured once and replayed; "
                           "launch shapes from wn_autotune_batch; median of 7 replays (min, max and spread beside it)"}

@@ -772,7 +772,18 @@ wn_status enqueue_batch(wn_stream *s, const std::vector<Group> &groups, void *ou
 {
     WN_CU(cudaMemsetAsync(d.queue, 0, sizeof(uint32_t) * 16, cs));
     WN_CU(cudaEventRecord(s->fork, cs));
+    // chain groups in the chain mode first (enqueued, not ordered: a graph
+    // whose throughput groups waited for the chain CTAs to begin -- a
+    // launch-completion event -- replayed back to back at 30-33 ms instead of
+    // 22.3, as if the edge waited for the chain kernel's end)
+    std::vector<char> chain_mode(groups.size(), 0);
     for (size_t gi = 0; gi < groups.size(); ++gi) {
+        uint32_t cg = 0;
+        chain_mode[gi] = groups[gi].exclusive && chain_default(groups[gi].N, cg) && chain_fits(s, groups[gi].N, cg);
+    }
+    for (int pass = 0; pass < 2; ++pass)
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        if ((pass == 0) != (chain_mode[gi] != 0)) continue;
         const Group &g = groups[gi];
         cudaStream_t b = g.exclusive ? s->branch_hi[gi] : s->branch[gi];
         WN_CU(cudaStreamWaitEvent(b, s->fork, 0));
@@ -802,7 +813,7 @@ wn_status enqueue_batch(wn_stream *s, const std::vector<Group> &groups, void *ou
                                           : (tuned != s->group_lat.end() ? tuned->second
                                                                          : s->batch_lat >= 2 && !batch_cfg(s, g.N).grp);
         uint32_t cg = 0;
-        if (g.exclusive && chain_default(g.N, cg) && chain_fits(s, g.N, cg)) {
+        if (chain_mode[gi] && chain_default(g.N, cg)) {
             // the longest chains: the chain mode, at most batch_density CTAs per SM
             const size_t csm = chain_smem(s, wn::chain_smem_bytes(s->smem_base, g.N, cg, g.r_max));
             switch (dt) {
@@ -1750,10 +1761,12 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
             if (!s->var && latency_default(g.N, lc)) all_lat[g.N] = true;
         }
         const size_t nplan = cands.size();
-        // median time of `reps` replays of the batch under plan ci (after one
-        // untimed); the groups' CTAs reach the SMs in a different order on
-        // every run, so single replays vary by ~10%
-        auto score = [&](size_t ci, int reps, float &t_ms) {
+        // time of `reps` replays of the batch under plan ci (after one
+        // untimed): their median, or with `worst` their slowest.  The groups'
+        // CTAs reach the SMs in a different order on every run, and a chain
+        // CTA that finds every SM taken waits for one to drain, so a plan can
+        // be fast on most replays and much slower on some
+        auto score = [&](size_t ci, int reps, float &t_ms, bool worst) {
             const auto &cd = cands[ci % nplan];
             s->group_lat = ci >= nplan ? all_lat : tuned_lat;
             s->batch_density = cd.second;
@@ -1776,22 +1789,23 @@ wn_status wn_autotune_batch(void *out, const uint64_t *counts, const uint64_t *o
             if (e != cudaSuccess || st != WN_OK || times.empty()) return false;
             std::sort(times.begin(), times.end());
             const size_t m = times.size();
-            t_ms = (m % 2) ? times[m / 2] : 0.5f * (times[m / 2 - 1] + times[m / 2]);
+            t_ms = worst ? times.back() : (m % 2) ? times[m / 2] : 0.5f * (times[m / 2 - 1] + times[m / 2]);
             return true;
         };
-        // every plan on four replays; then the best three again on eight, so
-        // that one lucky score does not decide
+        // every plan on four replays (median); then the best four again on
+        // eight, ranked by their slowest replay, so that neither one lucky
+        // score nor a plan that is only sometimes fast decides
         std::vector<std::pair<float, size_t>> scored;
         for (size_t ci = 0; ci < 2 * nplan && e == cudaSuccess && st == WN_OK; ++ci) {
             if (ci >= nplan && all_lat == tuned_lat) break;  // nothing different to try
             float t = 0.f;
-            if (score(ci, 4, t)) scored.push_back({t, ci});
+            if (score(ci, 4, t, false)) scored.push_back({t, ci});
         }
         std::sort(scored.begin(), scored.end());
         float best_ms = 1e30f;
-        for (size_t r = 0; r < scored.size() && r < 3 && e == cudaSuccess && st == WN_OK; ++r) {
+        for (size_t r = 0; r < scored.size() && r < 4 && e == cudaSuccess && st == WN_OK; ++r) {
             float t = 0.f;
-            if (!score(scored[r].second, 8, t) || t >= best_ms) continue;
+            if (!score(scored[r].second, 8, t, true) || t >= best_ms) continue;
             best_ms = t;
             best_crit = cands[scored[r].second % nplan].first;
             best_density = cands[scored[r].second % nplan].second;

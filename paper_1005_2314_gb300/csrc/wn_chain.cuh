@@ -603,8 +603,12 @@ __global__ void __launch_bounds__(chain_threads(G), 1) persist_chain_kernel(GenA
 // Compiled chain-mode shapes {pool N, compute warps G, quadruples per lane}.
 // (At most eight compute warps: with the two helpers no SM sub-partition
 // holds more than three warps, and the registers allow 64 values per lane.)
+#ifndef WN_DEBUG
 constexpr int kChainShapes[][3] = {{1024, 4, 2}, {1024, 8, 1}, {2048, 8, 2},
                                    {4096, 8, 4},  {8192, 8, 8}, {16384, 8, 16}};
+#else
+constexpr int kChainShapes[][3] = {{1024, 4, 2}};  // the debug build compiles one
+#endif
 
 template <int G, int QT, typename OutT>
 cudaError_t launch_chain_shape(const GenArgs &a, size_t smem, cudaStream_t cs)
