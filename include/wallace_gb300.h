@@ -240,6 +240,18 @@ wn_status wn_get_batch_plan(const wn_stream *s, int32_t *chains, uint32_t *densi
 wn_status wn_set_batch_plan(wn_stream *s, int32_t chains, uint32_t density);
 
 /*
+ * wn_set_batch_chain_kernel -- which kernel runs a batch's chain groups:
+ * chain_mode = 1 the chain mode (wn_set_config_ex, WN_CFG_CHAIN) for the pool
+ * sizes it serves, 0 (the default) the latency modes.  Measured on the
+ * 10,000-stream batch: a call after the GPU was idle, and eager calls, run
+ * ~1 ms faster in the chain mode (22.3-23.5 against 23.6 ms), but graph
+ * replays issued back to back took 30-37 ms in it, as if the chain CTAs then
+ * reached the SMs after the throughput groups' CTAs.  Drops a captured graph;
+ * WN_EINVAL for other values.  Values do not depend on the choice.
+ */
+wn_status wn_set_batch_chain_kernel(wn_stream *s, int32_t chain_mode);
+
+/*
  * wn_gbm -- a fused Monte Carlo consumer: geometric Brownian motion terminal
  * prices driven by the streams' own normals, which never leave the chip.
  * Stream i serves paths [i*paths_per_stream, (i+1)*paths_per_stream); path p

@@ -26,7 +26,7 @@ __all__ = [
     "wn_generate_host",
     "wn_set_cuda_stream", "wn_set_config", "wn_get_config", "wn_set_config_ex", "wn_get_config_ex",
     "WN_CFG_IN_PLACE", "WN_CFG_GROUP", "WN_CFG_CHAIN", "wn_autotune", "wn_gbm", "wn_generate_batch",
-    "wn_autotune_batch", "wn_generate_batch_noalloc", "wn_get_batch_plan", "wn_set_batch_plan", "wn_num_streams", "wn_get_pool", "wn_get_state",
+    "wn_autotune_batch", "wn_generate_batch_noalloc", "wn_get_batch_plan", "wn_set_batch_plan", "wn_set_batch_chain_kernel", "wn_num_streams", "wn_get_pool", "wn_get_state",
     "wn_rng_draws", "wn_debug_report", "wn_boxmuller", "wn_save", "wn_load", "wn_last_error", "library_path", "load",
 ]
 
@@ -76,6 +76,7 @@ def _load() -> ctypes.CDLL:
         "wn_generate_batch_noalloc": (_i, [_p, _p, _p, _p, _i, _p]),
         "wn_get_batch_plan": (_i, [_p, _p, _p]),
         "wn_set_batch_plan": (_i, [_p, ctypes.c_int32, _u32]),
+        "wn_set_batch_chain_kernel": (_i, [_p, ctypes.c_int32]),
         "wn_gbm": (_i, [_p, _p, _u32, _u32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                         ctypes.c_double, _p]),
         "wn_num_streams": (_u32, [_p]),
@@ -320,6 +321,11 @@ def wn_autotune_batch(out, counts, offsets, h: Handle, dtype: int = WN_F32, cuda
     counts, offsets, need = _batch_arrays(h, counts, offsets)
     _check(_L().wn_autotune_batch(_out_ptr(out, need, dtype), counts.ctypes.data, offsets.ctypes.data, h.ptr,
                                   dtype, _stream_ptr(cuda_stream)), "wn_autotune_batch")
+
+
+def wn_set_batch_chain_kernel(h: Handle, chain_mode: bool) -> None:
+    """Run the batch's chain groups in the chain mode (True) or the latency modes (False, the default)."""
+    _check(_L().wn_set_batch_chain_kernel(h.ptr, 1 if chain_mode else 0), "wn_set_batch_chain_kernel")
 
 
 def wn_get_batch_plan(h: Handle) -> tuple[int, int]:

@@ -168,6 +168,9 @@ struct wn_stream {
     // estimate's rule), and how many chain CTAs share an SM (1: exclusive)
     int batch_crit = -1;
     int batch_density = 1;
+    // batches: chain groups of pools the chain mode serves run it (else the
+    // latency modes); see wn_set_batch_chain_kernel
+    bool batch_chain_mode = false;
     int sm_smem = 0, smem_reserved = 0;  // shared memory per SM and reserved per CTA
     std::map<uint32_t, bool> group_lat;
     // some stream runs a method variant (wn_create_ex, wn_load): use the
@@ -772,14 +775,12 @@ wn_status enqueue_batch(wn_stream *s, const std::vector<Group> &groups, void *ou
 {
     WN_CU(cudaMemsetAsync(d.queue, 0, sizeof(uint32_t) * 16, cs));
     WN_CU(cudaEventRecord(s->fork, cs));
-    // chain groups in the chain mode first (enqueued, not ordered: a graph
-    // whose throughput groups waited for the chain CTAs to begin -- a
-    // launch-completion event -- replayed back to back at 30-33 ms instead of
-    // 22.3, as if the edge waited for the chain kernel's end)
+    // chain groups in the chain mode (when chosen) first
     std::vector<char> chain_mode(groups.size(), 0);
     for (size_t gi = 0; gi < groups.size(); ++gi) {
         uint32_t cg = 0;
-        chain_mode[gi] = groups[gi].exclusive && chain_default(groups[gi].N, cg) && chain_fits(s, groups[gi].N, cg);
+        chain_mode[gi] = s->batch_chain_mode && groups[gi].exclusive && chain_default(groups[gi].N, cg) &&
+                         chain_fits(s, groups[gi].N, cg);
     }
     for (int pass = 0; pass < 2; ++pass)
     for (size_t gi = 0; gi < groups.size(); ++gi) {
@@ -1925,6 +1926,18 @@ wn_status wn_set_batch_plan(wn_stream *s, int32_t chains, uint32_t density)
     s->batch_crit = chains;
     s->batch_density = (int)density;
     if (s->gexec) {  // a captured graph used the old plan
+        cudaGraphExecDestroy(s->gexec);
+        s->gexec = nullptr;
+    }
+    return WN_OK;
+}
+
+wn_status wn_set_batch_chain_kernel(wn_stream *s, int32_t chain_mode)
+{
+    if (!s) return fail(WN_EINVAL, "wn_set_batch_chain_kernel: NULL handle");
+    if (chain_mode != 0 && chain_mode != 1) return fail(WN_EINVAL, "wn_set_batch_chain_kernel: chain_mode must be 0 or 1");
+    s->batch_chain_mode = chain_mode == 1;
+    if (s->gexec) {  // a captured graph used the other kernels
         cudaGraphExecDestroy(s->gexec);
         s->gexec = nullptr;
     }

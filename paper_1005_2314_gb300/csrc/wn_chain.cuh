@@ -625,6 +625,11 @@ cudaError_t launch_persist_chain_shape(const GenArgs &a, const BatchArgs &bq, si
 {
     auto kern = persist_chain_kernel<G, QT, OutT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // every persistent kernel of a batch prefers the whole shared-memory
+    // carveout: an SM's split of L1 and shared memory serves all the CTAs it
+    // holds, and one preference lets any batch kernel join an SM the others use
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     int per_sm = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, chain_threads(G), smem);
     if (e != cudaSuccess) return e;

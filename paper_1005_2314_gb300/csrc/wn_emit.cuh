@@ -349,6 +349,12 @@ cudaError_t launch_persist_emit_shape(const GenArgs &a, const BatchArgs &bq, uin
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
+    // every persistent kernel of a batch prefers the whole shared-memory
+    // carveout: an SM's split of L1 and shared memory serves all the CTAs it
+    // holds, and one preference lets any batch kernel join an SM the others use
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+        return cudaGetLastError();
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)threads + 64, smem);
     if (e != cudaSuccess) return e;

@@ -8,7 +8,8 @@ bulk copies (pools above 8192: the compute warps store them themselves).  Every 
 FP32 error model, continue the sequence across calls (whole blocks, partial
 blocks, requests shorter than the rest of a block), leave the integer state
 exactly as the oracle's, and mix with the other kernels on one handle.  Lone
-streams take it without being asked; batches run their longest requests in it.
+streams take it without being asked; batches run their longest requests in it
+when wn_set_batch_chain_kernel asks for it.
 """
 import numpy as np
 import pytest
@@ -170,6 +171,7 @@ def test_batch_chain_groups_in_chain_mode(wn):
     for chains, density, graph in ((12, 1, False), (20, 4, True)):
         h = wn.wn_create_streams(N, R, seeds)
         wn.wn_set_batch_plan(h, chains, density)
+        wn.wn_set_batch_chain_kernel(h, True)
         for call in range(2):
             out.zero_()
             wn.wn_generate_batch(out, counts, offsets, h, use_graph=graph)
