@@ -431,6 +431,8 @@ def run_ours(args, rank, world, local_rank):
                 "algorithmic_bytes_per_launch": algo,
                 "kernel": (f"wn::group_kernel ({DT.upper()} out, {shape[1] // 32} warps x {shape[0]} quadruples "
                            f"per lane per stream, no control warp, in-place pool)" if shape[2] & 2 else
+                           f"wn::chain_kernel ({DT.upper()} out, {shape[1] // 32} compute warps x {shape[0]} "
+                           f"quadruples per lane + scale, store and draw warps per stream)" if shape[2] & 4 else
                            f"wn::generate_kernel ({DT.upper()} out, {shape[0]} quadruples x {shape[1]} compute "
                            f"threads + 1 control warp per stream{', in-place pool' if shape[2] else ''})")}
     if args.method == "boxmuller":
