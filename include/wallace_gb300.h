@@ -314,12 +314,12 @@ wn_status wn_set_config(wn_stream *s, uint32_t quads_per_thread, uint32_t thread
 /*
  * WN_CFG_CHAIN selects the chain-mode kernel, built for streams whose serial
  * chain of blocks sets the time (Section 5.1: each block's pool is the
- * previous block's output): threads / 32 compute warps run a stream's
- * passes, each drawing its own permutations and signs one pass ahead, on two
- * shared pool buffers (one barrier per pass); a further warp forms each
- * block's scale (Section 5.5) from the block's sums of squares while the
- * compute warps already run the next block, and a block's values are stored
- * during the next block's first pass.  quads_per_thread is the quadruples
+ * previous block's output): threads / 32 compute warps run only a stream's
+ * passes (one barrier per pass), while helper warps draw the passes'
+ * permutations and signs blocks ahead (Sections 5.2, 5.4, 5.8), form each
+ * block's scale from its sums of squares (Section 5.5) and write each block's
+ * values (for pools up to 8192 staged in shared memory and written with bulk
+ * copies).  quads_per_thread is the quadruples
  * per lane, with 128 * quads_per_thread * (threads / 32) = pool_N; compiled
  * for (pool 1024: 2, 128 and 1, 256), (2048: 2, 256), (4096: 4, 256),
  * (8192: 8, 256), (16384: 16, 256).  Launches of few streams of one

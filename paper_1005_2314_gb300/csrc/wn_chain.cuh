@@ -74,9 +74,9 @@ __host__ __device__ inline uint32_t chain_window(uint32_t base, uint32_t N, uint
     const uint32_t sz = 4u * N;
     return (base + chain_small(G) + sz - 1u) / sz * sz;
 }
-// Pools up to 8192 values have four pool buffers (two work buffers, two
-// emission buffers) and two staging buffers: a block's N - 1 values and up to
-// 7 carried ones, at 4 bytes at most.
+// Pools up to 8192 values have two work buffers, the emission buffers and a
+// staging buffer per store warp: a block's N - 1 values behind up to 7
+// positions of its first 16-byte chunk, at 4 bytes at most.
 __host__ __device__ constexpr bool chain_stages(uint32_t N) { return N <= 8192u; }
 __host__ __device__ constexpr uint32_t chain_stage_bytes(uint32_t N) { return ((N + 8u) * 4u + 15u) / 16u * 16u; }
 // Emission buffers: four up to pools of 4096 (a store warp may finish
@@ -220,7 +220,7 @@ template <> __device__ __forceinline__ void stage4<__half>(uint32_t a, float x, 
     stage4_16(a, __floats2half2_rn(x, y), __floats2half2_rn(z, w));
 }
 
-// A staged value (its output-type bits) read back, and stored as such.
+// A staged value (its output-type bits) read back, and stored to global memory as such.
 template <typename OutT> __device__ __forceinline__ uint32_t stage_ld(uint32_t a)
 {
     uint32_t v;
@@ -234,16 +234,6 @@ template <typename OutT> __device__ __forceinline__ uint32_t stage_ld(uint32_t a
         v = h;
     }
     return v;
-}
-template <typename OutT> __device__ __forceinline__ void stage_st(uint32_t a, uint32_t v)
-{
-    if (sizeof(OutT) == 4) {
-        if (!dbg_shared_ok(a, 4)) return;
-        asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v));
-    } else {
-        if (!dbg_shared_ok(a, 2)) return;
-        asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"((unsigned short)v));
-    }
 }
 template <typename OutT> __device__ __forceinline__ void global_st(const DbgRange &rg, OutT *p, uint32_t v)
 {
@@ -566,8 +556,8 @@ __device__ __forceinline__ void run_stream_chain(StreamHdr *__restrict__ h, floa
     }
 }
 
-// Chain-mode generate kernel: one CTA of G compute warps and three helper
-// warps per stream.  One CTA per SM is what a lone stream needs; the register
+// Chain-mode generate kernel: one CTA of G compute warps and the scale, store
+// and draw warps per stream.  One CTA per SM is what a lone stream needs; the register
 // bound follows from the thread count alone.
 template <int G, int QT, typename OutT>
 __global__ void __launch_bounds__(chain_threads(G), 1) chain_kernel(GenArgs a)
@@ -601,8 +591,8 @@ __global__ void __launch_bounds__(chain_threads(G), 1) persist_chain_kernel(GenA
 }
 
 // Compiled chain-mode shapes {pool N, compute warps G, quadruples per lane}.
-// (At most eight compute warps: with the two helpers no SM sub-partition
-// holds more than three warps, and the registers allow 64 values per lane.)
+// (At most eight compute warps: with the helpers no SM sub-partition holds
+// more than three warps, and the registers allow 64 values per lane.)
 #ifndef WN_DEBUG
 constexpr int kChainShapes[][3] = {{1024, 4, 2}, {1024, 8, 1}, {2048, 8, 2},
                                    {4096, 8, 4},  {8192, 8, 8}, {16384, 8, 16}};

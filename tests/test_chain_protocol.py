@@ -1,7 +1,7 @@
 """Model of the chain mode's hand-offs (wn_chain.cuh), checked on the CPU.
 
-The compute warps, the scale warp and the two store warps (blocks of even and
-of odd index) are actors stepped in random order.  Named barriers have the hardware's semantics: every arrival
+The compute warps, the scale warp, the store warps (store warp s takes the
+blocks b = s mod NS) and the draw warp are actors stepped in random order.  Named barriers have the hardware's semantics: every arrival
 (bar.arrive or bar.sync) counts towards the current phase, the phase
 completes at the barrier's count, and a bar.sync returns once the phase it
 arrived in has completed.  Bulk copies complete their reads at random later

@@ -1,10 +1,10 @@
 """Chain-mode kernel (WN_CFG_CHAIN) against the FP64 oracle.
 
-The chain mode runs a stream's passes on compute warps that draw their own
-permutations and signs one pass ahead, while a scale warp forms each block's
-scale from the block's sums of squares a whole block late and a store warp
-stages each block's values in the output's 16-byte layout and writes them with
-bulk copies (pools above 8192: the compute warps store them themselves).  Every compiled shape must return each stream's next values within the
+The chain mode runs a stream's passes on compute warps alone, while a draw
+warp writes the passes' permutation and sign words blocks ahead, a scale warp
+forms each block's scale from the block's sums of squares a block late, and
+store warps stage each block's values in the output's 16-byte layout and write
+them with bulk copies (pools above 8192: the compute warps store them).  Every compiled shape must return each stream's next values within the
 FP32 error model, continue the sequence across calls (whole blocks, partial
 blocks, requests shorter than the rest of a block), leave the integer state
 exactly as the oracle's, and mix with the other kernels on one handle.  Lone
